@@ -1,0 +1,329 @@
+"""Benchmark of the ATON step on the 512^3 lognormal workload (one JSON line on rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--grid 512]
+
+A step is one full radiative step: M1 transport with the Lax-Friedrichs flux, source
+injection, sub-cycled chemistry/cooling/absorption and the photon tallies, for every cell.
+Metric: cell-updates per second (grid cells x steps / time). Inputs are resident in HBM when
+the timed region starts; the state (7.0 GB read+write per 512^3 step) is far larger than L2,
+so no flush is needed between steps.
+
+N > 1 (torchrun): every rank advances its own replica of the workload (the method does not
+shard here); value = all ranks' cell-updates / max-over-ranks time ("weak" scaling).
+--impl reference times the FP64 CPU oracle on the host cores (bounded sample per step).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "M1+chemistry cell-updates/s at 512^3; % of HBM roofline; surrogate speedup"
+UNIT = "cell-updates/s"
+BYTES_PER_CELL = 52.0   # read N,Fx,Fy,Fz,y,T,nH (28 B) + write N,Fx,Fy,Fz,y,T (24 B)
+HBM_FALLBACK_GBS = 6400.0
+# DRAM bytes per cell-update of the fused kernel from an ncu capture, keyed by the hash of the
+# kernel sources it was taken on (the figure is dropped when the kernel changes).
+NCU_TRAFFIC = {}
+
+
+def kernel_hash():
+    h = hashlib.sha1()
+    for f in ("aton_kernels.cu", "aton_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1004_2503_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload(grid):
+    from paper_1004_2503_b300 import workloads as W
+    if grid == 512:
+        return W.workload_512(), ("lognormal n_H (sigma_ln=2.0, P(k)~k^-2.5, seed 3), 4096 sources "
+                                  "at the highest peaks (log-uniform 1e50-1e52 /s, seed 4), "
+                                  "dx=4 kpc, periodic, T0=100 K, x0=1e-4")
+    st = W.cosmo_box(grid, 2.0, max(1, 4096 * grid ** 3 // 512 ** 3), 3, 4)
+    return st, f"lognormal {grid}^3 (sigma_ln=2.0), scaled source count"
+
+
+def cpu_sample(st, idx, rate, run, budget_cells):
+    """Crop a periodic cube of the workload with about ``budget_cells`` cells (the CPU sample)."""
+    from paper_1004_2503_b300 import workloads as W
+    n = run["nx"]
+    side = int(max(16, min(n, round(budget_cells ** (1 / 3) / 8) * 8)))
+    # centre the crop on the brightest source so it holds fronts as well as neutral gas
+    k, j, i = np.unravel_index(int(idx[np.argmax(rate)]), st["N"].shape)
+    org = tuple(int(min(max(v - side // 2, 0), n - side)) for v in (k, j, i))
+    cst, cidx, crate = W.subsample_state(st, idx, rate, (side, side, side), org)
+    crun = dict(run, nx=side, ny=side, nz=side)
+    return cst, cidx, crate, crun, side, org
+
+
+def time_oracle(cst, cidx, crate, crun, steps, omp=False):
+    import oracle as O
+    p = O.params(c=crun["c"], dx=crun["dx"], dt=crun["dt"], sigma_n=crun["sigma_n"],
+                 sigma_e=crun["sigma_e"], e_gamma_eV=crun["e_gamma_eV"], bc=O.BC_PERIODIC)
+    t0 = time.perf_counter()
+    O.run(p, cst, steps, cidx, crate, omp=omp)
+    dt = time.perf_counter() - t0
+    return cst["N"].size * steps / dt, dt
+
+
+def reference_arm(args, world, rank):
+    if rank != 0:
+        return
+    (st, idx, rate, run), desc = workload(args.grid)
+    total = max(1, args.steps + args.warmup)
+    # about 90 s of single-core oracle work in total (about 1 us per cell-update)
+    cst, cidx, crate, crun, side, org = cpu_sample(st, idx, rate, run, 9e7 / total)
+    import oracle as O
+    p = O.params(c=crun["c"], dx=crun["dx"], dt=crun["dt"], sigma_n=crun["sigma_n"],
+                 sigma_e=crun["sigma_e"], e_gamma_eV=crun["e_gamma_eV"], bc=O.BC_PERIODIC)
+    cur = cst
+    for _ in range(args.warmup):
+        cur, _, _ = O.run(p, cur, 1, cidx, crate)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cur, _, _ = O.run(p, cur, 1, cidx, crate)
+    dt = time.perf_counter() - t0
+    v = cst["N"].size * args.steps / dt
+    sample = f"{side}^3 periodic crop at {org} of the {args.grid}^3 workload, one step per step"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": desc, "grid": args.grid, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def ours(args, world, rank, local):
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1004_2503_b300 import aton as A
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    (st, idx, rate, run), desc = workload(args.grid)
+    ncell = st["N"].size
+    stream = torch.cuda.Stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    def maxtime(t):
+        if dist is None:
+            return t
+        x = torch.tensor([t], device="cuda", dtype=torch.float64)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        return float(x.item())
+
+    a = A.from_workload(st, idx, rate, run)
+    a.set_stream(stream)
+    ty, tz, tune_ms = a.autotune(3)
+    a.set_exec(A.MODE_FUSED, args.graph_batch)
+    a.step(args.warmup)
+    a.synchronize()
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    a.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    barrier()
+    clk = clocks.stop()
+    t = maxtime(e0.elapsed_time(e1) / 1e3)
+    rc = a.synchronize()
+    diag = a.diag()
+    bud = a.photon_budget()
+    launches = a.launches_per_step() * args.steps
+    value = world * ncell * args.steps / t
+    ms = 1e3 * t / args.steps
+
+    # plain unfused three-kernel step at the same accuracy, from the same state
+    ku = max(3, min(args.steps, 200))
+    a.set_exec(A.MODE_UNFUSED, args.graph_batch)
+    a.step(3)
+    a.synchronize()
+    u0 = torch.cuda.Event(enable_timing=True)
+    u1 = torch.cuda.Event(enable_timing=True)
+    u0.record(stream)
+    a.step(ku)
+    u1.record(stream)
+    u1.synchronize()
+    tu = u0.elapsed_time(u1) / 1e3
+    unfused = {"value": ncell * ku / tu, "ms_per_step": 1e3 * tu / ku,
+               "launches_per_step": a.launches_per_step(), "steps": ku,
+               "achieved_gbs_at_52B": BYTES_PER_CELL * ncell * ku / tu / 1e9}
+    a.close()
+
+    # end to end through the C ABI with host buffers (pinned): state in, every step a source
+    # list in and the photon budget out, state out at the end
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).pin_memory().numpy()
+           for k, v in st.items()}
+    ypin = torch.from_numpy(np.ascontiguousarray(1.0 - st["x"], np.float32)).pin_memory().numpy()
+    outs = {k: torch.empty(st["N"].shape, dtype=torch.float32).pin_memory().numpy()
+            for k in ("N", "Fx", "Fy", "Fz", "y", "T")}
+    b = A.Aton(run["nx"], run["ny"], run["nz"], run["dx"], run["c"], run["dt"])
+    b.set_params(bc=A.BC_PERIODIC, sigma_n=run["sigma_n"], sigma_e=run["sigma_e"],
+                 e_gamma_eV=run["e_gamma_eV"])
+    b.set_tile(ty, tz)
+    b.set_exec(A.MODE_FUSED, args.graph_batch)
+    b.set_fields(pin["N"], pin["Fx"], pin["Fy"], pin["Fz"], pin["T"], pin["nH"], y=ypin)
+    b.add_sources(idx, rate)
+    b.step(1)
+    b.photon_budget()
+    barrier()
+    t0 = time.perf_counter()
+    b.set_fields(pin["N"], pin["Fx"], pin["Fy"], pin["Fz"], pin["T"], pin["nH"], y=ypin)
+    for _ in range(args.steps):
+        b.add_sources(idx, rate)
+        b.step(1)
+        b.photon_budget()
+    b.get_fields(out=outs)
+    barrier()
+    te = maxtime(time.perf_counter() - t0)
+    b.close()
+    h2d = (7 * 4 * ncell) / args.steps + (8 + 8) * len(idx)
+    d2h = 6 * 8 + (6 * 4 * ncell) / args.steps
+    e2e = {"value": world * ncell * args.steps / te, "unit": UNIT,
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+           "what": "set_fields(host, pinned) once + per step add_sources(host) + aton_step(1) "
+                   "+ aton_photon_budget(host) + get_fields(host) once"}
+
+    peak, peak_kind = peaks()
+    achieved = BYTES_PER_CELL * ncell / (t / args.steps) / 1e9
+    kh = kernel_hash()
+    traffic = NCU_TRAFFIC.get(kh)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "grid": args.grid, "cells": ncell, "sources": len(idx),
+                   "mode": "fused", "graph_batch": args.graph_batch, "tile_ty_tz": [ty, tz],
+                   "autotune_ms_per_step": tune_ms, "parallelism": f"replicas x{world}",
+                   "l2": "no flush: 7.0 GB of state per step >> 126 MB L2"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_kind,
+                     "traffic": None if traffic is None else traffic * ncell,
+                     "kernel": "k_fused", "bytes_per_cell_update": BYTES_PER_CELL,
+                     "kernel_hash": kh},
+        "unfused": unfused,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "status": rc,
+        "diag": diag,
+        "budget_closure": (bud["stored0"] + bud["emitted"] - bud["stored"] - bud["absorbed"] -
+                           bud["escaped"] - bud["clipped"]) / max(bud["emitted"], 1e-300),
+    }
+    if rank == 0 and not args.no_cpu:
+        cst, cidx, crate, crun, side, org = cpu_sample(st, idx, rate, run, 2.5e6)
+        v1, d1 = time_oracle(cst, cidx, crate, crun, 4)
+        vo, do = time_oracle(cst, cidx, crate, crun, 4, omp=True)
+        line["cpu_baseline"] = {
+            "value": v1, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"4 steps of a {side}^3 periodic crop at {org} of the same workload "
+                      f"({d1:.1f} s)",
+            "omp": {"value": vo, "cores": os.cpu_count(), "seconds": do}}
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--grid", type=int, default=512)
+    ap.add_argument("--graph-batch", type=int, default=100)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        reference_arm(args, world, rank)
+    else:
+        ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

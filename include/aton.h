@@ -1,0 +1,196 @@
+/*
+ * aton.h -- C ABI of the B300 ATON step library (libaton.so).
+ *
+ * One explicit time step of the ATON method (Aubert & Teyssier 2010): moment transport of a
+ * single-group ionising photon field (density N, flux F) with the M1 closure and the
+ * Lax-Friedrichs intercell flux (section 2.2, Eqs. 3-7; Appendix Eqs. A1-A3, A5), point-source
+ * injection (section 2.3: sources act as per-cell emission, nearest grid point), then the
+ * sub-cycled hydrogen photo-chemistry, photo-heating and cooling with photon absorption, the
+ * operator Phi of Appendix Eq. A4 (section 2.2, chemistry paragraph; section 3.2.1, Eq. 14).
+ *
+ * Conventions shared by every entry point:
+ *  - Units are cgs at the boundary: N [photons cm^-3], F [photons cm^-2 s^-1], T [K],
+ *    nH [cm^-3], rates [photons s^-1], budgets [photons].
+ *  - Fields are dense 3-D arrays in C order with x fastest: idx = i + nx*(j + ny*k), float32.
+ *  - Every array argument is copied; the library never keeps a caller pointer. `where`
+ *    (ATON_HOST / ATON_DEVICE) says whether the pointers are host memory (pageable or pinned)
+ *    or device memory on the handle's device.
+ *  - The handle owns all device memory it allocates and frees it in aton_finalize.
+ *  - Work is queued on the handle's stream. Calls that return data to the host synchronise
+ *    that stream; aton_step does not.
+ *  - Return 0 on success or a negative ATON_ERR_* code; aton_strerror() describes it and
+ *    aton_last_message() gives the detail of the last failure on this thread.
+ *  - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef ATON_H
+#define ATON_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define ATON_OK 0
+#define ATON_ERR_BADARG (-1)    /* invalid argument: size, pointer, index, or dt above the CFL limit */
+#define ATON_ERR_NOMEM (-2)     /* device or host allocation failed */
+#define ATON_ERR_CUDA (-3)      /* a CUDA runtime/driver call failed (detail in aton_last_message) */
+#define ATON_ERR_SUBCYCLE (-4)  /* a cell reached the chemistry sub-cycle cap (state kept, flagged) */
+#define ATON_ERR_NONFINITE (-5) /* a non-finite value was produced or supplied */
+#define ATON_ERR_STATE (-6)     /* call out of order (e.g. stepping before aton_set_fields) */
+
+/* ---- enumerations ---- */
+#define ATON_HOST 0
+#define ATON_DEVICE 1
+#define ATON_BC_PERIODIC 0
+#define ATON_BC_TRANSMISSIVE 1
+#define ATON_SRC_REPLACE 0
+#define ATON_SRC_APPEND 1
+#define ATON_MODE_FUSED 0      /* one fused transport+source+chemistry kernel per step */
+#define ATON_MODE_UNFUSED 1    /* plain three-kernel step (transport; sources; chemistry) */
+
+/* photon-budget vector returned by aton_photon_budget [photons] */
+#define ATON_B_EMITTED 0   /* sum of Ndot dt injected by the sources */
+#define ATON_B_STORED 1    /* sum of N V now on the grid */
+#define ATON_B_ABSORBED 2  /* photons absorbed by photo-ionisations */
+#define ATON_B_ESCAPED 3   /* net photons that left through transmissive faces */
+#define ATON_B_CLIPPED 4   /* N removed by the N >= 0 clamp (<= 0: photons added) */
+#define ATON_B_STORED0 5   /* sum of N V when the fields were last set */
+#define ATON_BUDGET_LEN 6
+/* identity: stored0 + emitted = stored + absorbed + escaped + clipped */
+
+typedef struct aton_ctx* aton_handle;
+
+/* Physical and numerical parameters. Defaults (aton_default_params) are the paper's single
+ * group for a 50 000 K black body (section 2.2: sigma_e 2.49e-18, sigma_n 2.93e-18 cm^2,
+ * e 20.27 eV), periodic boundaries, evolving temperature with cooling and collisional
+ * ionisation, sub-step fraction 0.1 and a cap of 10 000 sub-steps. */
+typedef struct {
+  double sigma_n;     /* number-averaged H photo-ionisation cross-section [cm^2] */
+  double sigma_e;     /* energy-averaged cross-section [cm^2] */
+  double e_gamma_eV;  /* mean ionising photon energy [eV] */
+  int bc;             /* ATON_BC_* */
+  int fixed_T;        /* nonzero: temperature is not evolved */
+  int coll_ion;       /* nonzero: collisional ionisation and its cooling */
+  int cooling;        /* nonzero: radiative cooling */
+  int max_sub;        /* chemistry sub-cycle cap per radiative step (>= 1) */
+  double T_floor;     /* temperature floor [K] (> 0) */
+  double sub_eps;     /* allowed relative change of y = 1-x and of T per sub-step (0, 1] */
+  double y_floor;     /* floor of y in the sub-step criterion (> 0) */
+  double clump_R_A, clump_R_b; /* recombination clumping C_R = max(1, A nH^b); A = 0: off
+                                  (section 3.2.1, Eq. 15, read with C_R on the
+                                  recombination term and C_I on photo-ionisation) */
+  double clump_I_A, clump_I_b; /* photo-ionisation clumping C_I = max(1, A nH^b); A = 0: off */
+} aton_params;
+
+/* Counters accumulated since aton_set_fields. */
+typedef struct {
+  int64_t steps;            /* radiative steps taken */
+  int64_t substeps_total;   /* chemistry sub-steps summed over cells and steps */
+  int64_t substeps_max;     /* largest sub-step count of any cell in any step */
+  int64_t error_cells;      /* cell-steps that reached the sub-cycle cap */
+  int64_t nonfinite_cells;  /* cell-steps that produced a non-finite value */
+} aton_diag;
+
+/* Fills *p with the defaults above. Never fails. */
+void aton_default_params(aton_params* p);
+
+/* Creates a handle for an nx*ny*nz grid of cubic cells of size dx_cm, speed of light c_cms
+ * (a reduced value is allowed) and radiative step dt_s, on the current CUDA device.
+ * The explicit scheme needs dt < dx/c (section 2.2, Eq. 7); the unsplit 3-D Lax-Friedrichs
+ * update used here is positive only for 3 c dt / dx <= 1, which is enforced.
+ * Allocates the device state (double-buffered N, F; y, T, nH) and a stream.
+ * Errors: BADARG (sizes < 1, cell count above 2^31-1, non-positive dx/c/dt, 3 c dt/dx > 1,
+ * out == NULL), NOMEM, CUDA. On error *out is set to NULL. */
+int aton_init(int nx, int ny, int nz, double dx_cm, double c_cms, double dt_s, aton_handle* out);
+
+/* Releases every resource of the handle (NULL is ignored). */
+void aton_finalize(aton_handle h);
+
+/* Replaces the parameters. Validated (BADARG on out-of-range values). Takes effect at the
+ * next aton_step. */
+int aton_set_params(aton_handle h, const aton_params* p);
+int aton_get_params(aton_handle h, aton_params* p);
+
+/* Runs the work of this handle on an existing CUDA stream (cudaStream_t cast to void*; NULL
+ * restores the handle's own stream). The caller keeps ownership of the stream and must keep
+ * it alive while the handle uses it. */
+int aton_set_stream(aton_handle h, void* stream);
+
+/* Chooses the kernel path: ATON_MODE_FUSED (default) or ATON_MODE_UNFUSED, and the number of
+ * steps captured in one CUDA graph (0: no graphs, plain launches). */
+int aton_set_exec(aton_handle h, int mode, int graph_batch);
+
+/* Sets the tile of the fused kernel: ty rows of 32 cells per CTA and tz planes per z-slab.
+ * ty in {4, 8, 16}; tz >= 1. */
+int aton_set_tile(aton_handle h, int ty, int tz);
+
+/* Times the fused kernel on a scratch copy of the current state for each candidate tile and
+ * keeps the fastest (the simulation state is not advanced). `steps` per candidate (>= 1).
+ * Writes the chosen (ty, tz) and its time per step [ms] when the pointers are not NULL. */
+int aton_autotune(aton_handle h, int steps, int* ty_out, int* tz_out, float* ms_out);
+
+/* Copies the state in (section 2.2: energy density, flux, temperature, ionisation fraction
+ * and baryon density, the per-cell quantities of the Appendix). N, Fx, Fy, Fz, T, nH are
+ * required; the ionisation state is given either as the neutral fraction y (preferred:
+ * stored as is, no cancellation near full ionisation) or as the ionised fraction x
+ * (converted y = 1 - x on the device); exactly one of x, y must be non-NULL.
+ * Resets the photon budget and the counters; stored0 becomes sum N V.
+ * Errors: BADARG (NULL pointers, both/neither of x,y, bad where), NONFINITE (a non-finite or
+ * negative N, T <= 0, nH <= 0, y outside [0,1]: checked on the device), CUDA. */
+int aton_set_fields(aton_handle h, const float* N, const float* Fx, const float* Fy,
+                    const float* Fz, const float* x, const float* y, const float* T,
+                    const float* nH, int where);
+
+/* Copies the current state out. Any output pointer may be NULL (skipped). x and y are the
+ * ionised and neutral fractions. Synchronises the stream. Errors: BADARG, STATE, CUDA. */
+int aton_get_fields(aton_handle h, float* N, float* Fx, float* Fy, float* Fz, float* x,
+                    float* y, float* T, int where);
+
+/* Sets (REPLACE) or extends (APPEND) the point-source list: cell_idx[s] in [0, ncell) (linear
+ * index as above), rate_per_s[s] >= 0 photons/s. Host arrays. Sources in the same cell are
+ * summed. Each step adds rate*dt/V to N of its cell after transport and before chemistry
+ * (section 2.3 nearest-grid-point emission; S in Eq. 3 and Appendix Eq. A2).
+ * Errors: BADARG (index out of range, negative or non-finite rate, n < 0, bad mode). */
+int aton_add_sources(aton_handle h, const int64_t* cell_idx, const double* rate_per_s,
+                     int64_t n, int mode);
+
+/* Queues nsteps radiative steps on the handle's stream (asynchronous). Each step is the
+ * transport of (N, F) from the old state, the clamp N >= 0, |F| <= cN, source injection and
+ * the chemistry/cooling/absorption operator per cell. Errors: BADARG (nsteps < 0), STATE
+ * (fields not set), CUDA (launch failure), or a SUBCYCLE/NONFINITE status latched by an
+ * earlier synchronising call. */
+int aton_step(aton_handle h, int nsteps);
+
+/* Waits for queued work and returns its status: ATON_ERR_SUBCYCLE or ATON_ERR_NONFINITE if a
+ * cell was flagged since the last aton_set_fields, else OK or a CUDA error. */
+int aton_synchronize(aton_handle h);
+
+/* Returns the photon budget [photons], indices ATON_B_*; out must hold ATON_BUDGET_LEN
+ * doubles. Reductions are FP64 and in a fixed order (deterministic). Synchronises. */
+int aton_photon_budget(aton_handle h, double* out);
+
+/* Restores a budget saved by aton_photon_budget (checkpoint/restart); the STORED entry is
+ * ignored (it is recomputed from the fields). */
+int aton_set_budget(aton_handle h, const double* in);
+
+/* Counters since aton_set_fields (synchronises). */
+int aton_get_diag(aton_handle h, aton_diag* out);
+
+/* Number of cell-steps flagged SUBCYCLE or NONFINITE since aton_set_fields (synchronises). */
+int aton_last_error_cells(aton_handle h, int64_t* count);
+
+/* Number of kernel launches per radiative step of the current execution mode. */
+int aton_launches_per_step(aton_handle h, int* launches);
+
+/* Static description of a status code. */
+const char* aton_strerror(int code);
+
+/* Detail of the last failure on the calling thread ("" if none). */
+const char* aton_last_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

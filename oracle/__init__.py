@@ -69,6 +69,9 @@ def lib(omp=False):
         L.orc_run.restype = C.c_int
         L.orc_run.argtypes = ([C.POINTER(Params), C.c_int, C.c_int, C.c_int, C.c_int] + [_D] * 7 +
                               [C.c_int64, _I64, _D, C.POINTER(Budget), C.POINTER(Stats)])
+        L.orc_cell_step.restype = C.c_int
+        L.orc_cell_step.argtypes = ([C.POINTER(Params)] + [_D] * 4 +
+                                    [C.c_double] * 4 + [_D])
         L.orc_stored.restype = C.c_double
         L.orc_stored.argtypes = [C.POINTER(Params), C.c_int64, _D]
         _LIBS[key] = L
@@ -183,3 +186,13 @@ def run(p, state, nsteps, src_idx=None, src_rate=None, omp=False, budget=None, s
 def stored(p, N):
     N = _f64(N)
     return lib().orc_stored(C.byref(p), N.size, _ptr(N))
+
+
+def cell_step(p, N27, Fx27, Fy27, Fz27, x, T, nH, src_rate=0.0):
+    """One step of the centre of a 3x3x3 neighbourhood (ghosts pre-filled by the caller).
+    Returns dict(N, Fx, Fy, Fz, x, T, absorbed, err)."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (N27, Fx27, Fy27, Fz27)]
+    out = np.zeros(7)
+    err = lib().orc_cell_step(C.byref(p), *(_ptr(a) for a in arrs), float(x), float(T),
+                              float(nH), float(src_rate), _ptr(out))
+    return dict(zip(("N", "Fx", "Fy", "Fz", "x", "T", "absorbed"), out), err=err)

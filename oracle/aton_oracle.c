@@ -213,7 +213,7 @@ void orc_transport(const orc_params* p, int nx, int ny, int nz,
  * Chemistry, cooling and absorption: the operator Phi of Appendix Eq. A4 on one cell.
  * Section 2.2 (chemistry paragraph): hydrogen only, explicit sub-cycling inside the radiative
  * step "in the spirit of Anninos et al. (1997)"; absorption -kappa N, -kappa F of Eqs. 3-4;
- * the ionisation balance of Eq. 14, -nH dx/dt = alpha nH^2 x^2 - (1-x) nH Gamma, written for
+ * the ionisation balance of section 3.2.1 Eq. 14, -nH dx/dt = alpha nH^2 x^2 - (1-x) nH Gamma, written for
  * y = 1 - x, with Gamma = c sigma_n N and case-B alpha, plus collisional ionisation.
  *
  * Each sub-step h takes the backward-difference (creation/destruction) form of Anninos et al.
@@ -402,4 +402,41 @@ double orc_stored(const orc_params* p, int64_t ncell, const double* N) {
   double s = 0.0;
   for (int64_t i = 0; i < ncell; ++i) s += N[i] * V;
   return s;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * The same step for one cell from its 3x3x3 neighbourhood (used to check sampled cells of
+ * grids too large for a whole-grid oracle run): transport of the centre with the
+ * Lax-Friedrichs flux (Appendix Eq. A2 in 3-D), clamp, source, operator Phi (Eq. A4).
+ * ------------------------------------------------------------------------------------------ */
+int orc_cell_step(const orc_params* p, const double* N27, const double* Fx27, const double* Fy27,
+                  const double* Fz27, double x, double T, double nH, double src_rate, double out[7]) {
+  const double c = p->c, lam = p->dt / p->dx, V = p->dx * p->dx * p->dx;
+  const int ctr = 13;
+  const int step[3] = {1, 3, 9};
+  double u[4] = {N27[ctr], Fx27[ctr], Fy27[ctr], Fz27[ctr]};
+  double acc[4] = {0, 0, 0, 0};
+  for (int d = 0; d < 3; ++d) {
+    int ip = ctr + step[d], im = ctr - step[d];
+    double up[4] = {N27[ip], Fx27[ip], Fy27[ip], Fz27[ip]};
+    double um[4] = {N27[im], Fx27[im], Fy27[im], Fz27[im]};
+    double fp[4], fm[4];
+    orc_lf_flux(d, u, up, c, fp);
+    orc_lf_flux(d, um, u, c, fm);
+    for (int q = 0; q < 4; ++q) acc[q] += fp[q] - fm[q];
+  }
+  double N = u[0] - lam * acc[0], Fx = u[1] - lam * acc[1], Fy = u[2] - lam * acc[2],
+         Fz = u[3] - lam * acc[3];
+  if (N < 0.0) {
+    N = 0.0; Fx = 0.0; Fy = 0.0; Fz = 0.0;
+  } else {
+    double Fn = sqrt(Fx * Fx + Fy * Fy + Fz * Fz);
+    if (Fn > c * N) { double s = c * N / Fn; Fx *= s; Fy *= s; Fz *= s; }
+  }
+  N += src_rate * p->dt / V;
+  double ab = 0.0;
+  int64_t ns = 0;
+  int e = orc_chem_cell(p, nH, &N, &Fx, &Fy, &Fz, &x, &T, &ab, &ns);
+  out[0] = N; out[1] = Fx; out[2] = Fy; out[3] = Fz; out[4] = x; out[5] = T; out[6] = ab;
+  return e;
 }

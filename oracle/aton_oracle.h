@@ -87,6 +87,12 @@ int orc_run(const orc_params* p, int nx, int ny, int nz, int nsteps,
 
 double orc_stored(const orc_params* p, int64_t ncell, const double* N);
 
+/* One full step of the centre cell of a 3x3x3 neighbourhood (index 13 = centre, x fastest),
+ * whose ghost values the caller has already filled by the boundary rule: transport, clamp,
+ * source Ndot (photons/s) and chemistry. out = {N, Fx, Fy, Fz, x, T, absorbed per volume}. */
+int orc_cell_step(const orc_params* p, const double* N27, const double* Fx27, const double* Fy27,
+                  const double* Fz27, double x, double T, double nH, double src_rate, double out[7]);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,282 @@
+"""Thin ctypes binding of libaton.so (include/aton.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels. Arrays are passed either as
+NumPy float32 arrays (host) or as contiguous float32 torch CUDA tensors (device); nothing is
+computed here. If the library is missing, loading raises instead of falling back to anything.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libaton.so")
+
+OK = 0
+ERR_BADARG, ERR_NOMEM, ERR_CUDA, ERR_SUBCYCLE, ERR_NONFINITE, ERR_STATE = -1, -2, -3, -4, -5, -6
+HOST, DEVICE = 0, 1
+BC_PERIODIC, BC_TRANSMISSIVE = 0, 1
+SRC_REPLACE, SRC_APPEND = 0, 1
+MODE_FUSED, MODE_UNFUSED = 0, 1
+B_EMITTED, B_STORED, B_ABSORBED, B_ESCAPED, B_CLIPPED, B_STORED0 = range(6)
+BUDGET_LEN = 6
+BUDGET_KEYS = ("emitted", "stored", "absorbed", "escaped", "clipped", "stored0")
+
+# every entry point declared in include/aton.h
+EXPORTS = (
+    "aton_default_params", "aton_init", "aton_finalize", "aton_set_params", "aton_get_params",
+    "aton_set_stream", "aton_set_exec", "aton_set_tile", "aton_autotune", "aton_set_fields",
+    "aton_get_fields", "aton_add_sources", "aton_step", "aton_synchronize",
+    "aton_photon_budget", "aton_set_budget", "aton_get_diag", "aton_last_error_cells",
+    "aton_launches_per_step", "aton_strerror", "aton_last_message",
+)
+
+
+class aton_params(C.Structure):
+    _fields_ = [
+        ("sigma_n", C.c_double), ("sigma_e", C.c_double), ("e_gamma_eV", C.c_double),
+        ("bc", C.c_int), ("fixed_T", C.c_int), ("coll_ion", C.c_int), ("cooling", C.c_int),
+        ("max_sub", C.c_int),
+        ("T_floor", C.c_double), ("sub_eps", C.c_double), ("y_floor", C.c_double),
+        ("clump_R_A", C.c_double), ("clump_R_b", C.c_double),
+        ("clump_I_A", C.c_double), ("clump_I_b", C.c_double),
+    ]
+
+
+class aton_diag(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("substeps_total", C.c_int64),
+                ("substeps_max", C.c_int64), ("error_cells", C.c_int64),
+                ("nonfinite_cells", C.c_int64)]
+
+
+class AtonError(RuntimeError):
+    def __init__(self, code, where, msg):
+        super().__init__(f"{where}: {msg} (status {code})")
+        self.code = code
+
+
+_lib = None
+_VP = C.c_void_p
+
+
+def load():
+    """Load libaton.so (built by paper_1004_2503_b300.build); raise if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with `python -m paper_1004_2503_b300.build` "
+            "(there is no CPU fallback)")
+    L = C.CDLL(LIB_PATH)
+    L.aton_default_params.argtypes = [C.POINTER(aton_params)]
+    L.aton_default_params.restype = None
+    L.aton_init.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                            C.POINTER(_VP)]
+    L.aton_finalize.argtypes = [_VP]
+    L.aton_finalize.restype = None
+    L.aton_set_params.argtypes = [_VP, C.POINTER(aton_params)]
+    L.aton_get_params.argtypes = [_VP, C.POINTER(aton_params)]
+    L.aton_set_stream.argtypes = [_VP, _VP]
+    L.aton_set_exec.argtypes = [_VP, C.c_int, C.c_int]
+    L.aton_set_tile.argtypes = [_VP, C.c_int, C.c_int]
+    L.aton_autotune.argtypes = [_VP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                C.POINTER(C.c_float)]
+    L.aton_set_fields.argtypes = [_VP] + [_VP] * 8 + [C.c_int]
+    L.aton_get_fields.argtypes = [_VP] + [_VP] * 7 + [C.c_int]
+    L.aton_add_sources.argtypes = [_VP, _VP, _VP, C.c_int64, C.c_int]
+    L.aton_step.argtypes = [_VP, C.c_int]
+    L.aton_synchronize.argtypes = [_VP]
+    L.aton_photon_budget.argtypes = [_VP, C.POINTER(C.c_double)]
+    L.aton_set_budget.argtypes = [_VP, C.POINTER(C.c_double)]
+    L.aton_get_diag.argtypes = [_VP, C.POINTER(aton_diag)]
+    L.aton_last_error_cells.argtypes = [_VP, C.POINTER(C.c_int64)]
+    L.aton_launches_per_step.argtypes = [_VP, C.POINTER(C.c_int)]
+    L.aton_strerror.argtypes = [C.c_int]
+    L.aton_strerror.restype = C.c_char_p
+    L.aton_last_message.argtypes = []
+    L.aton_last_message.restype = C.c_char_p
+    for name in EXPORTS:
+        fn = getattr(L, name)
+        if fn.restype is C.c_int or name in ("aton_init",):
+            fn.restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(code, where):
+    if code != OK:
+        L = load()
+        raise AtonError(code, where, (L.aton_last_message() or b"").decode() or
+                        L.aton_strerror(code).decode())
+    return code
+
+
+def default_params():
+    p = aton_params()
+    load().aton_default_params(C.byref(p))
+    return p
+
+
+def _ptr(a, where):
+    """(pointer, where) of a float32 NumPy array or torch CUDA tensor; None passes NULL."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float32 or not a.flags.c_contiguous:
+            raise TypeError("host arrays must be C-contiguous float32")
+        return a.ctypes.data
+    # torch tensor
+    if getattr(a, "is_cuda", False):
+        import torch
+        if a.dtype != torch.float32 or not a.is_contiguous():
+            raise TypeError("device tensors must be contiguous float32")
+        return a.data_ptr()
+    raise TypeError("expected a NumPy array or a torch CUDA tensor")
+
+
+def _where(arrays):
+    dev = [getattr(a, "is_cuda", False) for a in arrays if a is not None]
+    if all(dev):
+        return DEVICE
+    if not any(dev):
+        return HOST
+    raise TypeError("mix of host and device arrays")
+
+
+class Aton:
+    """One simulation handle (aton_init ... aton_finalize)."""
+
+    def __init__(self, nx, ny, nz, dx, c, dt):
+        self.L = load()
+        h = _VP()
+        _check(self.L.aton_init(int(nx), int(ny), int(nz), float(dx), float(c), float(dt),
+                                C.byref(h)), "aton_init")
+        self.h = h
+        self.shape = (int(nz), int(ny), int(nx))
+        self.ncell = int(nx) * int(ny) * int(nz)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.aton_finalize(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- configuration
+    def set_params(self, **kw):
+        p = aton_params()
+        _check(self.L.aton_get_params(self.h, C.byref(p)), "aton_get_params")
+        for k, v in kw.items():
+            if not hasattr(p, k):
+                raise KeyError(k)
+            setattr(p, k, v)
+        _check(self.L.aton_set_params(self.h, C.byref(p)), "aton_set_params")
+
+    def get_params(self):
+        p = aton_params()
+        _check(self.L.aton_get_params(self.h, C.byref(p)), "aton_get_params")
+        return {k: getattr(p, k) for k, _ in aton_params._fields_}
+
+    def set_stream(self, stream):
+        ptr = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+        _check(self.L.aton_set_stream(self.h, ptr), "aton_set_stream")
+
+    def set_exec(self, mode=MODE_FUSED, graph_batch=100):
+        _check(self.L.aton_set_exec(self.h, int(mode), int(graph_batch)), "aton_set_exec")
+
+    def set_tile(self, ty, tz):
+        _check(self.L.aton_set_tile(self.h, int(ty), int(tz)), "aton_set_tile")
+
+    def autotune(self, steps=3):
+        ty, tz, ms = C.c_int(), C.c_int(), C.c_float()
+        _check(self.L.aton_autotune(self.h, int(steps), C.byref(ty), C.byref(tz), C.byref(ms)),
+               "aton_autotune")
+        return ty.value, tz.value, ms.value
+
+    # -- state
+    def set_fields(self, N, Fx, Fy, Fz, T, nH, x=None, y=None):
+        arrs = (N, Fx, Fy, Fz, x, y, T, nH)
+        for a in arrs:
+            if a is not None and int(np.prod(a.shape)) != self.ncell:
+                raise ValueError("field size does not match the grid")
+        w = _where(arrs)
+        _check(self.L.aton_set_fields(self.h, *(_ptr(a, w) for a in arrs), w), "aton_set_fields")
+
+    def get_fields(self, out=None, device=False):
+        """Returns dict(N, Fx, Fy, Fz, x, y, T): host float32 arrays, or the given ``out`` dict
+        of preallocated arrays/tensors, or new torch CUDA tensors when device=True."""
+        keys = ("N", "Fx", "Fy", "Fz", "x", "y", "T")
+        if out is None:
+            if device:
+                import torch
+                out = {k: torch.empty(self.shape, dtype=torch.float32, device="cuda") for k in keys}
+            else:
+                out = {k: np.empty(self.shape, np.float32) for k in keys}
+        arrs = [out.get(k) for k in keys]
+        w = _where(arrs)
+        _check(self.L.aton_get_fields(self.h, *(_ptr(a, w) for a in arrs), w), "aton_get_fields")
+        return out
+
+    def add_sources(self, cell_idx, rate, mode=SRC_REPLACE):
+        i = np.ascontiguousarray(cell_idx, dtype=np.int64)
+        r = np.ascontiguousarray(rate, dtype=np.float64)
+        if i.shape != r.shape:
+            raise ValueError("cell_idx and rate differ in length")
+        _check(self.L.aton_add_sources(self.h, i.ctypes.data, r.ctypes.data, i.size, int(mode)),
+               "aton_add_sources")
+
+    # -- stepping
+    def step(self, nsteps=1):
+        _check(self.L.aton_step(self.h, int(nsteps)), "aton_step")
+
+    def synchronize(self):
+        return self.L.aton_synchronize(self.h)
+
+    def photon_budget(self):
+        b = (C.c_double * BUDGET_LEN)()
+        _check(self.L.aton_photon_budget(self.h, b), "aton_photon_budget")
+        return dict(zip(BUDGET_KEYS, list(b)))
+
+    def set_budget(self, budget):
+        b = (C.c_double * BUDGET_LEN)(*[float(budget[k]) for k in BUDGET_KEYS])
+        _check(self.L.aton_set_budget(self.h, b), "aton_set_budget")
+
+    def diag(self):
+        d = aton_diag()
+        _check(self.L.aton_get_diag(self.h, C.byref(d)), "aton_get_diag")
+        return {k: getattr(d, k) for k, _ in aton_diag._fields_}
+
+    def last_error_cells(self):
+        n = C.c_int64()
+        _check(self.L.aton_last_error_cells(self.h, C.byref(n)), "aton_last_error_cells")
+        return n.value
+
+    def launches_per_step(self):
+        n = C.c_int()
+        _check(self.L.aton_launches_per_step(self.h, C.byref(n)), "aton_launches_per_step")
+        return n.value
+
+
+def from_workload(state, src_idx, src_rate, run, **params):
+    """Create a handle for a workload tuple of ``workloads`` and load its state (host)."""
+    a = Aton(run["nx"], run["ny"], run["nz"], run["dx"], run["c"], run["dt"])
+    bc = BC_TRANSMISSIVE if run["bc"] == "transmissive" else BC_PERIODIC
+    kw = dict(bc=bc, sigma_n=run["sigma_n"], sigma_e=run["sigma_e"], e_gamma_eV=run["e_gamma_eV"])
+    kw.update(params)
+    a.set_params(**kw)
+    f32 = {k: np.ascontiguousarray(v, dtype=np.float32) for k, v in state.items()}
+    y = np.ascontiguousarray(1.0 - np.asarray(state["x"], np.float64), dtype=np.float32)
+    a.set_fields(f32["N"], f32["Fx"], f32["Fy"], f32["Fz"], f32["T"], f32["nH"], y=y)
+    a.add_sources(src_idx, src_rate)
+    return a

@@ -1,0 +1,761 @@
+// aton_capi.cu -- host implementation of the C ABI declared in include/aton.h.
+//
+// The handle owns the device state (double-buffered N, F; y = 1 - x, T, nH in place),
+// the per-tile tally slots, the point-source lists (merged per cell, and bucketed per fused
+// tile), and a cache of CUDA graphs that each replay a batch of steps. The host only queues
+// work (section 2.2 and the Appendix: the host drives the time loop and never computes on the
+// data); it reads back only when a call returns data.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "aton_internal.h"
+
+using namespace aton;
+
+static thread_local std::string g_msg;
+
+static int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_msg = buf;
+  return code;
+}
+
+#define CU(call)                                                                    \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return fail(e_ == cudaErrorMemoryAllocation ? ATON_ERR_NOMEM : ATON_ERR_CUDA, \
+                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+static constexpr double kEV = 1.602176634e-12;
+static constexpr double kKBh = 1.380649e-16;
+static constexpr double kIH = 13.6;  // eV
+
+struct aton_ctx {
+  int nx = 0, ny = 0, nz = 0;
+  int64_t ncell = 0;
+  double dx = 0, c = 0, dt = 0, V = 0;
+  aton_params prm{};
+  int device = 0;
+  cudaStream_t own = nullptr, user = nullptr;
+  float* f[2][4] = {{nullptr}};
+  float *y = nullptr, *T = nullptr, *nH = nullptr;
+  int cur = 0;
+  bool fields_set = false;
+  // reductions
+  double* d_part = nullptr;
+  double* d_out = nullptr;            // [4]: acc3 + stored
+  unsigned long long* d_u64 = nullptr;  // [4]
+  unsigned int* d_bad = nullptr;
+  Slots slots;
+  // folded tallies (density units for the photon sums)
+  double fold_acc[3] = {0, 0, 0};
+  unsigned long long fold_u[4] = {0, 0, 0, 0};
+  double emitted = 0, stored0 = 0;
+  double offs[ATON_BUDGET_LEN] = {0};
+  int64_t steps = 0;
+  int latched = ATON_OK;
+  // sources
+  std::map<int64_t, double> src;  // merged: cell -> rate
+  double emit_per_step = 0;       // photons actually injected per step
+  int* d_src_idx = nullptr;
+  float* d_src_dN = nullptr;
+  int src_n = 0, src_cap = 0;
+  int* d_tstart = nullptr;
+  TileSrc* d_tsrc = nullptr;
+  int tstart_cap = 0, tsrc_cap = 0;
+  bool tiles_dirty = true;
+  // execution
+  int mode = ATON_MODE_FUSED;
+  int graph_batch = 100;
+  int ty = 8, tz = 64;
+  std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+
+  cudaStream_t stream() const { return user ? user : own; }
+};
+
+static int check_h(aton_handle h) {
+  if (!h) return fail(ATON_ERR_BADARG, "null handle");
+  return ATON_OK;
+}
+
+static void drop_graphs(aton_handle h) {
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+}
+
+static StepParams step_params(const aton_ctx* h) {
+  StepParams P{};
+  P.nx = h->nx; P.ny = h->ny; P.nz = h->nz;
+  P.bc = h->prm.bc;
+  P.lam = (float)(h->c * h->dt / h->dx);
+  P.c = (float)h->c;
+  P.rc = (float)(1.0 / h->c);
+  P.dt = (float)h->dt;
+  P.csig = (float)(h->c * h->prm.sigma_n);
+  const double eheat = (h->prm.sigma_e * h->prm.e_gamma_eV - h->prm.sigma_n * kIH) / h->prm.sigma_n;
+  P.eheat_K = (float)(eheat * kEV / kKBh);
+  P.fixed_T = h->prm.fixed_T != 0;
+  P.coll_ion = h->prm.coll_ion != 0;
+  P.cooling = h->prm.cooling != 0;
+  P.max_sub = h->prm.max_sub;
+  P.T_floor = (float)h->prm.T_floor;
+  P.sub_eps = (float)h->prm.sub_eps;
+  P.y_floor = (float)h->prm.y_floor;
+  P.clR_A = (float)h->prm.clump_R_A; P.clR_b = (float)h->prm.clump_R_b;
+  P.clI_A = (float)h->prm.clump_I_A; P.clI_b = (float)h->prm.clump_I_b;
+  return P;
+}
+
+static int slots_needed(const aton_ctx* h) {
+  return std::max(fused_tiles(h->nx, h->ny, h->nz, h->ty, h->tz), kPlainBlocks);
+}
+
+static void free_slots(Slots& s) {
+  cudaFree(s.acc); cudaFree(s.sub); cudaFree(s.mx); cudaFree(s.err); cudaFree(s.nan);
+  s = Slots{};
+}
+
+// Adds the slot tallies into the host fold (FP64, fixed order) and clears the slots.
+static int fold_slots(aton_handle h) {
+  if (h->slots.n == 0) return ATON_OK;
+  cudaStream_t s = h->stream();
+  CU(launch_reduce_slots(h->slots, h->d_out, h->d_u64, s));
+  double a[3];
+  unsigned long long u[4];
+  CU(cudaMemcpyAsync(a, h->d_out, sizeof(a), cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(u, h->d_u64, sizeof(u), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  for (int i = 0; i < 3; ++i) h->fold_acc[i] += a[i];
+  h->fold_u[0] += u[0];
+  h->fold_u[1] = std::max(h->fold_u[1], u[1]);
+  h->fold_u[2] += u[2];
+  h->fold_u[3] += u[3];
+  const int n = h->slots.n;
+  CU(cudaMemsetAsync(h->slots.acc, 0, sizeof(double) * 3 * n, s));
+  CU(cudaMemsetAsync(h->slots.sub, 0, sizeof(unsigned long long) * n, s));
+  CU(cudaMemsetAsync(h->slots.mx, 0, sizeof(unsigned int) * n, s));
+  CU(cudaMemsetAsync(h->slots.err, 0, sizeof(unsigned int) * n, s));
+  CU(cudaMemsetAsync(h->slots.nan, 0, sizeof(unsigned int) * n, s));
+  return ATON_OK;
+}
+
+static int ensure_slots_n(aton_handle h, int need) {
+  if (h->slots.n >= need) return ATON_OK;
+  int rc = fold_slots(h);
+  if (rc) return rc;
+  free_slots(h->slots);
+  drop_graphs(h);
+  Slots s;
+  CU(cudaMalloc(&s.acc, sizeof(double) * 3 * need));
+  CU(cudaMalloc(&s.sub, sizeof(unsigned long long) * need));
+  CU(cudaMalloc(&s.mx, sizeof(unsigned int) * need));
+  CU(cudaMalloc(&s.err, sizeof(unsigned int) * need));
+  CU(cudaMalloc(&s.nan, sizeof(unsigned int) * need));
+  s.n = need;
+  h->slots = s;
+  cudaStream_t st = h->stream();
+  CU(cudaMemsetAsync(s.acc, 0, sizeof(double) * 3 * need, st));
+  CU(cudaMemsetAsync(s.sub, 0, sizeof(unsigned long long) * need, st));
+  CU(cudaMemsetAsync(s.mx, 0, sizeof(unsigned int) * need, st));
+  CU(cudaMemsetAsync(s.err, 0, sizeof(unsigned int) * need, st));
+  CU(cudaMemsetAsync(s.nan, 0, sizeof(unsigned int) * need, st));
+  return ATON_OK;
+}
+
+static int ensure_slots(aton_handle h) { return ensure_slots_n(h, slots_needed(h)); }
+
+// Uploads the merged source list and the per-tile buckets of the current fused tile.
+static int upload_sources(aton_handle h) {
+  cudaStream_t s = h->stream();
+  const int n = (int)h->src.size();
+  std::vector<int> idx(n);
+  std::vector<float> dN(n);
+  double emit = 0;
+  int k = 0;
+  for (auto& kv : h->src) {
+    idx[k] = (int)kv.first;
+    dN[k] = (float)(kv.second * h->dt / h->V);
+    emit += (double)dN[k] * h->V;
+    ++k;
+  }
+  h->emit_per_step = emit;
+  if (n > h->src_cap) {
+    cudaFree(h->d_src_idx); cudaFree(h->d_src_dN);
+    h->d_src_idx = nullptr; h->d_src_dN = nullptr;
+    const int cap = std::max(n, 64);
+    CU(cudaMalloc(&h->d_src_idx, sizeof(int) * cap));
+    CU(cudaMalloc(&h->d_src_dN, sizeof(float) * cap));
+    h->src_cap = cap;
+    drop_graphs(h);
+  }
+  if (n > 0) {
+    CU(cudaMemcpyAsync(h->d_src_idx, idx.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(h->d_src_dN, dN.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s));
+  }
+  if (h->src_n != n) drop_graphs(h);  // the unfused source launch size is baked into graphs
+  h->src_n = n;
+  // per-tile buckets sorted by (tile, z)
+  const int gxn = (h->nx + kTileX - 1) / kTileX, gyn = (h->ny + h->ty - 1) / h->ty;
+  const int ntile = fused_tiles(h->nx, h->ny, h->nz, h->ty, h->tz);
+  std::vector<std::pair<long long, TileSrc>> ent;
+  ent.reserve(n);
+  k = 0;
+  for (auto& kv : h->src) {
+    const int64_t c = kv.first;
+    const int i = (int)(c % h->nx), j = (int)((c / h->nx) % h->ny), z = (int)(c / ((int64_t)h->nx * h->ny));
+    const int bx = i / kTileX, by = j / h->ty, bz = z / h->tz;
+    const long long tile = bx + (long long)gxn * (by + (long long)gyn * bz);
+    TileSrc t{z, (i - bx * kTileX) + kTileX * (j - by * h->ty), dN[k], 0};
+    ent.push_back({tile * (long long)h->nz + z, t});
+    ++k;
+  }
+  std::sort(ent.begin(), ent.end(), [](const auto& a, const auto& b) {
+    return a.first < b.first || (a.first == b.first && a.second.cell < b.second.cell);
+  });
+  std::vector<int> start(ntile + 1, 0);
+  std::vector<TileSrc> ts(std::max(n, 1));
+  for (int e = 0; e < n; ++e) {
+    start[ent[e].first / h->nz + 1] += 1;
+    ts[e] = ent[e].second;
+  }
+  for (int t = 0; t < ntile; ++t) start[t + 1] += start[t];
+  if (ntile + 1 > h->tstart_cap) {
+    cudaFree(h->d_tstart);
+    h->d_tstart = nullptr;
+    CU(cudaMalloc(&h->d_tstart, sizeof(int) * (ntile + 1)));
+    h->tstart_cap = ntile + 1;
+    drop_graphs(h);
+  }
+  if (std::max(n, 1) > h->tsrc_cap) {
+    cudaFree(h->d_tsrc);
+    h->d_tsrc = nullptr;
+    const int cap = std::max(n, 64);
+    CU(cudaMalloc(&h->d_tsrc, sizeof(TileSrc) * cap));
+    h->tsrc_cap = cap;
+    drop_graphs(h);
+  }
+  CU(cudaMemcpyAsync(h->d_tstart, start.data(), sizeof(int) * (ntile + 1), cudaMemcpyHostToDevice, s));
+  if (n > 0) CU(cudaMemcpyAsync(h->d_tsrc, ts.data(), sizeof(TileSrc) * n, cudaMemcpyHostToDevice, s));
+  h->tiles_dirty = false;
+  return ATON_OK;
+}
+
+static int enqueue_step(aton_handle h, cudaStream_t s) {
+  const int nxt = 1 - h->cur;
+  const Fields in{h->f[h->cur][0], h->f[h->cur][1], h->f[h->cur][2], h->f[h->cur][3]};
+  const Fields out{h->f[nxt][0], h->f[nxt][1], h->f[nxt][2], h->f[nxt][3]};
+  cudaError_t e;
+  if (h->mode == ATON_MODE_FUSED) {
+    FusedArgs a{};
+    a.P = step_params(h);
+    a.in = in; a.out = out;
+    a.y = h->y; a.T = h->T; a.nH = h->nH;
+    a.tsrc_start = h->d_tstart; a.tsrc = h->d_tsrc;
+    a.slots = h->slots;
+    a.tz = h->tz;
+    e = launch_fused(h->ty, a, s);
+  } else {
+    PlainArgs a{};
+    a.P = step_params(h);
+    a.in = in; a.out = out;
+    a.y = h->y; a.T = h->T; a.nH = h->nH;
+    a.src_idx = h->d_src_idx; a.src_dN = h->d_src_dN; a.nsrc = h->src_n;
+    a.slots = h->slots;
+    e = launch_plain_step(a, s);
+  }
+  if (e != cudaSuccess) return fail(ATON_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
+  h->cur = nxt;
+  return ATON_OK;
+}
+
+static int prepare(aton_handle h) {
+  if (!h->fields_set) return fail(ATON_ERR_STATE, "aton_set_fields has not been called");
+  int rc = ensure_slots(h);
+  if (rc) return rc;
+  if (h->tiles_dirty) {
+    rc = upload_sources(h);
+    if (rc) return rc;
+  }
+  return ATON_OK;
+}
+
+extern "C" {
+
+void aton_default_params(aton_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->sigma_n = 2.93e-18;
+  p->sigma_e = 2.49e-18;
+  p->e_gamma_eV = 20.27;
+  p->bc = ATON_BC_PERIODIC;
+  p->fixed_T = 0;
+  p->coll_ion = 1;
+  p->cooling = 1;
+  p->max_sub = 10000;
+  p->T_floor = 1.0;
+  p->sub_eps = 0.1;
+  p->y_floor = 1e-6;
+}
+
+const char* aton_strerror(int code) {
+  switch (code) {
+    case ATON_OK: return "ok";
+    case ATON_ERR_BADARG: return "invalid argument";
+    case ATON_ERR_NOMEM: return "out of memory";
+    case ATON_ERR_CUDA: return "CUDA error";
+    case ATON_ERR_SUBCYCLE: return "chemistry sub-cycle cap reached in some cells";
+    case ATON_ERR_NONFINITE: return "non-finite or out-of-range field values";
+    case ATON_ERR_STATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+const char* aton_last_message(void) { return g_msg.c_str(); }
+
+void aton_finalize(aton_handle h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->stream()) cudaStreamSynchronize(h->stream());
+  drop_graphs(h);
+  for (int b = 0; b < 2; ++b)
+    for (int q = 0; q < 4; ++q) cudaFree(h->f[b][q]);
+  cudaFree(h->y); cudaFree(h->T); cudaFree(h->nH);
+  cudaFree(h->d_part); cudaFree(h->d_out); cudaFree(h->d_u64); cudaFree(h->d_bad);
+  free_slots(h->slots);
+  cudaFree(h->d_src_idx); cudaFree(h->d_src_dN); cudaFree(h->d_tstart); cudaFree(h->d_tsrc);
+  if (h->own) cudaStreamDestroy(h->own);
+  delete h;
+}
+
+int aton_init(int nx, int ny, int nz, double dx_cm, double c_cms, double dt_s, aton_handle* out) {
+  if (!out) return fail(ATON_ERR_BADARG, "out is NULL");
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1) return fail(ATON_ERR_BADARG, "grid sizes must be >= 1");
+  const int64_t ncell = (int64_t)nx * ny * nz;
+  if (ncell > 2147483647LL) return fail(ATON_ERR_BADARG, "more than 2^31-1 cells");
+  if (!(dx_cm > 0) || !(c_cms > 0) || !(dt_s > 0) || !std::isfinite(dx_cm) ||
+      !std::isfinite(c_cms) || !std::isfinite(dt_s))
+    return fail(ATON_ERR_BADARG, "dx, c and dt must be positive and finite");
+  const double cfl = 3.0 * c_cms * dt_s / dx_cm;
+  if (cfl > 1.0 + 1e-12)
+    return fail(ATON_ERR_BADARG, "3 c dt / dx = %.6g exceeds 1 (unsplit 3-D Lax-Friedrichs limit)", cfl);
+  aton_ctx* h = new aton_ctx();
+  h->nx = nx; h->ny = ny; h->nz = nz; h->ncell = ncell;
+  h->dx = dx_cm; h->c = c_cms; h->dt = dt_s; h->V = dx_cm * dx_cm * dx_cm;
+  aton_default_params(&h->prm);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    delete h;
+    return fail(ATON_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  }
+  h->device = dev;
+  static bool attrs_done = false;
+  if (!attrs_done) {
+    e = init_kernel_attributes();
+    if (e != cudaSuccess) {
+      delete h;
+      return fail(ATON_ERR_CUDA, "kernel attributes: %s", cudaGetErrorString(e));
+    }
+    attrs_done = true;
+  }
+  auto bail = [&](int rc) { aton_finalize(h); return rc; };
+  if (cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(fail(ATON_ERR_CUDA, "cudaStreamCreate failed"));
+  const size_t fb = sizeof(float) * (size_t)ncell;
+  for (int b = 0; b < 2; ++b)
+    for (int q = 0; q < 4; ++q)
+      if (cudaMalloc(&h->f[b][q], fb) != cudaSuccess)
+        return bail(fail(ATON_ERR_NOMEM, "cudaMalloc of %zu bytes failed", fb));
+  if (cudaMalloc(&h->y, fb) != cudaSuccess || cudaMalloc(&h->T, fb) != cudaSuccess ||
+      cudaMalloc(&h->nH, fb) != cudaSuccess)
+    return bail(fail(ATON_ERR_NOMEM, "cudaMalloc of %zu bytes failed", fb));
+  if (cudaMalloc(&h->d_part, sizeof(double) * kSumBlocks) != cudaSuccess ||
+      cudaMalloc(&h->d_out, sizeof(double) * 4) != cudaSuccess ||
+      cudaMalloc(&h->d_u64, sizeof(unsigned long long) * 4) != cudaSuccess ||
+      cudaMalloc(&h->d_bad, sizeof(unsigned int)) != cudaSuccess)
+    return bail(fail(ATON_ERR_NOMEM, "cudaMalloc of reduction scratch failed"));
+  h->tz = std::min(64, nz);
+  *out = h;
+  return ATON_OK;
+}
+
+int aton_set_params(aton_handle h, const aton_params* p) {
+  if (int rc = check_h(h)) return rc;
+  if (!p) return fail(ATON_ERR_BADARG, "params is NULL");
+  if (!(p->sigma_n > 0) || !(p->sigma_e >= 0) || !(p->e_gamma_eV >= 0))
+    return fail(ATON_ERR_BADARG, "cross-sections / photon energy out of range");
+  if (p->bc != ATON_BC_PERIODIC && p->bc != ATON_BC_TRANSMISSIVE)
+    return fail(ATON_ERR_BADARG, "bc must be ATON_BC_PERIODIC or ATON_BC_TRANSMISSIVE");
+  if (p->max_sub < 1) return fail(ATON_ERR_BADARG, "max_sub must be >= 1");
+  if (!(p->T_floor > 0) || !(p->sub_eps > 0 && p->sub_eps <= 1) || !(p->y_floor > 0))
+    return fail(ATON_ERR_BADARG, "T_floor, sub_eps or y_floor out of range");
+  if (!(p->clump_R_A >= 0) || !(p->clump_I_A >= 0) || !std::isfinite(p->clump_R_b) ||
+      !std::isfinite(p->clump_I_b))
+    return fail(ATON_ERR_BADARG, "clumping parameters out of range");
+  h->prm = *p;
+  drop_graphs(h);  // parameters are baked into captured launches
+  return ATON_OK;
+}
+
+int aton_get_params(aton_handle h, aton_params* p) {
+  if (int rc = check_h(h)) return rc;
+  if (!p) return fail(ATON_ERR_BADARG, "params is NULL");
+  *p = h->prm;
+  return ATON_OK;
+}
+
+int aton_set_stream(aton_handle h, void* stream) {
+  if (int rc = check_h(h)) return rc;
+  CU(cudaStreamSynchronize(h->stream()));
+  h->user = (cudaStream_t)stream;
+  return ATON_OK;
+}
+
+int aton_set_exec(aton_handle h, int mode, int graph_batch) {
+  if (int rc = check_h(h)) return rc;
+  if (mode != ATON_MODE_FUSED && mode != ATON_MODE_UNFUSED)
+    return fail(ATON_ERR_BADARG, "mode must be ATON_MODE_FUSED or ATON_MODE_UNFUSED");
+  if (graph_batch < 0) return fail(ATON_ERR_BADARG, "graph_batch must be >= 0");
+  if (mode != h->mode) {
+    if (int rc = fold_slots(h)) return rc;
+  }
+  h->mode = mode;
+  h->graph_batch = graph_batch;
+  drop_graphs(h);
+  return ATON_OK;
+}
+
+int aton_set_tile(aton_handle h, int ty, int tz) {
+  if (int rc = check_h(h)) return rc;
+  if (ty != 4 && ty != 8 && ty != 16) return fail(ATON_ERR_BADARG, "ty must be 4, 8 or 16");
+  if (tz < 1) return fail(ATON_ERR_BADARG, "tz must be >= 1");
+  tz = std::min(tz, h->nz);
+  if (ty == h->ty && tz == h->tz) return ATON_OK;
+  if (int rc = fold_slots(h)) return rc;
+  h->ty = ty;
+  h->tz = tz;
+  h->tiles_dirty = true;
+  drop_graphs(h);
+  return ATON_OK;
+}
+
+int aton_set_fields(aton_handle h, const float* N, const float* Fx, const float* Fy,
+                    const float* Fz, const float* x, const float* y, const float* T,
+                    const float* nH, int where) {
+  if (int rc = check_h(h)) return rc;
+  if (!N || !Fx || !Fy || !Fz || !T || !nH) return fail(ATON_ERR_BADARG, "NULL field pointer");
+  if ((x == nullptr) == (y == nullptr)) return fail(ATON_ERR_BADARG, "give exactly one of x, y");
+  if (where != ATON_HOST && where != ATON_DEVICE) return fail(ATON_ERR_BADARG, "bad where");
+  cudaStream_t s = h->stream();
+  const cudaMemcpyKind k = where == ATON_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const size_t fb = sizeof(float) * (size_t)h->ncell;
+  h->fields_set = false;
+  float** d = h->f[h->cur];
+  CU(cudaMemcpyAsync(d[0], N, fb, k, s));
+  CU(cudaMemcpyAsync(d[1], Fx, fb, k, s));
+  CU(cudaMemcpyAsync(d[2], Fy, fb, k, s));
+  CU(cudaMemcpyAsync(d[3], Fz, fb, k, s));
+  CU(cudaMemcpyAsync(h->y, x ? x : y, fb, k, s));
+  CU(cudaMemcpyAsync(h->T, T, fb, k, s));
+  CU(cudaMemcpyAsync(h->nH, nH, fb, k, s));
+  if (x) CU(launch_one_minus(h->y, h->y, h->ncell, s));
+  CU(cudaMemsetAsync(h->d_bad, 0, sizeof(unsigned int), s));
+  CU(launch_validate(d[0], h->y, h->T, h->nH, h->ncell, h->d_bad, s));
+  unsigned int bad = 0;
+  CU(cudaMemcpyAsync(&bad, h->d_bad, sizeof(bad), cudaMemcpyDeviceToHost, s));
+  CU(launch_sum_field(d[0], h->ncell, h->d_part, h->d_out + 3, s));
+  double st = 0;
+  CU(cudaMemcpyAsync(&st, h->d_out + 3, sizeof(st), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  if (bad) return fail(ATON_ERR_NONFINITE, "%u cells have non-finite or out-of-range values", bad);
+  // reset tallies
+  if (h->slots.n) {
+    if (int rc = fold_slots(h)) return rc;
+  }
+  std::memset(h->fold_acc, 0, sizeof(h->fold_acc));
+  std::memset(h->fold_u, 0, sizeof(h->fold_u));
+  std::memset(h->offs, 0, sizeof(h->offs));
+  h->emitted = 0;
+  h->steps = 0;
+  h->stored0 = st * h->V;
+  h->latched = ATON_OK;
+  h->fields_set = true;
+  return ATON_OK;
+}
+
+int aton_get_fields(aton_handle h, float* N, float* Fx, float* Fy, float* Fz, float* x, float* y,
+                    float* T, int where) {
+  if (int rc = check_h(h)) return rc;
+  if (where != ATON_HOST && where != ATON_DEVICE) return fail(ATON_ERR_BADARG, "bad where");
+  if (!h->fields_set) return fail(ATON_ERR_STATE, "aton_set_fields has not been called");
+  cudaStream_t s = h->stream();
+  const cudaMemcpyKind k = where == ATON_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  const size_t fb = sizeof(float) * (size_t)h->ncell;
+  float** d = h->f[h->cur];
+  float* scratch = h->f[1 - h->cur][0];  // the spare buffer is dead between steps
+  if (N) CU(cudaMemcpyAsync(N, d[0], fb, k, s));
+  float* outs[3] = {Fx, Fy, Fz};
+  for (int q = 0; q < 3; ++q)
+    if (outs[q]) CU(cudaMemcpyAsync(outs[q], d[q + 1], fb, k, s));
+  if (y) CU(cudaMemcpyAsync(y, h->y, fb, k, s));
+  if (x) {
+    CU(launch_one_minus(scratch, h->y, h->ncell, s));
+    CU(cudaMemcpyAsync(x, scratch, fb, k, s));
+  }
+  if (T) CU(cudaMemcpyAsync(T, h->T, fb, k, s));
+  CU(cudaStreamSynchronize(s));
+  return ATON_OK;
+}
+
+int aton_add_sources(aton_handle h, const int64_t* cell_idx, const double* rate, int64_t n, int mode) {
+  if (int rc = check_h(h)) return rc;
+  if (n < 0) return fail(ATON_ERR_BADARG, "n < 0");
+  if (n > 0 && (!cell_idx || !rate)) return fail(ATON_ERR_BADARG, "NULL source arrays");
+  if (mode != ATON_SRC_REPLACE && mode != ATON_SRC_APPEND) return fail(ATON_ERR_BADARG, "bad mode");
+  for (int64_t i = 0; i < n; ++i) {
+    if (cell_idx[i] < 0 || cell_idx[i] >= h->ncell)
+      return fail(ATON_ERR_BADARG, "source %lld: cell index %lld out of range", (long long)i,
+                  (long long)cell_idx[i]);
+    if (!(rate[i] >= 0) || !std::isfinite(rate[i]))
+      return fail(ATON_ERR_BADARG, "source %lld: rate must be finite and >= 0", (long long)i);
+  }
+  if (mode == ATON_SRC_REPLACE) h->src.clear();
+  for (int64_t i = 0; i < n; ++i) h->src[cell_idx[i]] += rate[i];
+  return upload_sources(h);
+}
+
+int aton_step(aton_handle h, int nsteps) {
+  if (int rc = check_h(h)) return rc;
+  if (nsteps < 0) return fail(ATON_ERR_BADARG, "nsteps < 0");
+  if (h->latched != ATON_OK) return h->latched;
+  if (int rc = prepare(h)) return rc;
+  cudaStream_t s = h->stream();
+  int left = nsteps;
+  while (left > 0) {
+    const int b = h->graph_batch > 0 ? std::min(left, h->graph_batch) : 1;
+    if (h->graph_batch > 0) {
+      auto key = std::make_pair(b, h->cur);
+      auto it = h->graphs.find(key);
+      if (it == h->graphs.end()) {
+        const int cur0 = h->cur;
+        CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        int rc = ATON_OK;
+        for (int i = 0; i < b && rc == ATON_OK; ++i) rc = enqueue_step(h, s);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        h->cur = cur0;
+        if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+        if (e != cudaSuccess) return fail(ATON_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        cudaGraphExec_t ge = nullptr;
+        e = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(ATON_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        it = h->graphs.emplace(key, ge).first;
+      }
+      CU(cudaGraphLaunch(it->second, s));
+      if (b & 1) h->cur = 1 - h->cur;
+    } else {
+      if (int rc = enqueue_step(h, s)) return rc;
+    }
+    h->steps += b;
+    h->emitted += h->emit_per_step * b;
+    left -= b;
+  }
+  return ATON_OK;
+}
+
+static int read_tallies(aton_handle h, double acc[3], unsigned long long u[4], double* stored) {
+  cudaStream_t s = h->stream();
+  double a[4] = {0, 0, 0, 0};
+  unsigned long long uu[4] = {0, 0, 0, 0};
+  if (h->slots.n) {
+    CU(launch_reduce_slots(h->slots, h->d_out, h->d_u64, s));
+  }
+  if (stored) CU(launch_sum_field(h->f[h->cur][0], h->ncell, h->d_part, h->d_out + 3, s));
+  CU(cudaMemcpyAsync(a, h->d_out, sizeof(a), cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(uu, h->d_u64, sizeof(uu), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  if (!h->slots.n) { a[0] = a[1] = a[2] = 0; uu[0] = uu[1] = uu[2] = uu[3] = 0; }
+  for (int i = 0; i < 3; ++i) acc[i] = h->fold_acc[i] + a[i];
+  u[0] = h->fold_u[0] + uu[0];
+  u[1] = std::max(h->fold_u[1], uu[1]);
+  u[2] = h->fold_u[2] + uu[2];
+  u[3] = h->fold_u[3] + uu[3];
+  if (stored) *stored = a[3];
+  if (u[3]) h->latched = ATON_ERR_NONFINITE;
+  else if (u[2]) h->latched = ATON_ERR_SUBCYCLE;
+  return ATON_OK;
+}
+
+int aton_synchronize(aton_handle h) {
+  if (int rc = check_h(h)) return rc;
+  CU(cudaStreamSynchronize(h->stream()));
+  if (!h->fields_set) return ATON_OK;
+  double acc[3];
+  unsigned long long u[4];
+  if (int rc = read_tallies(h, acc, u, nullptr)) return rc;
+  return h->latched;
+}
+
+int aton_photon_budget(aton_handle h, double* out) {
+  if (int rc = check_h(h)) return rc;
+  if (!out) return fail(ATON_ERR_BADARG, "out is NULL");
+  if (!h->fields_set) return fail(ATON_ERR_STATE, "aton_set_fields has not been called");
+  double acc[3], st = 0;
+  unsigned long long u[4];
+  if (int rc = read_tallies(h, acc, u, &st)) return rc;
+  out[ATON_B_EMITTED] = h->emitted + h->offs[ATON_B_EMITTED];
+  out[ATON_B_STORED] = st * h->V;
+  out[ATON_B_ABSORBED] = acc[0] * h->V + h->offs[ATON_B_ABSORBED];
+  out[ATON_B_ESCAPED] = acc[1] * h->V + h->offs[ATON_B_ESCAPED];
+  out[ATON_B_CLIPPED] = acc[2] * h->V + h->offs[ATON_B_CLIPPED];
+  out[ATON_B_STORED0] = h->stored0 + h->offs[ATON_B_STORED0];
+  return ATON_OK;
+}
+
+int aton_set_budget(aton_handle h, const double* in) {
+  if (int rc = check_h(h)) return rc;
+  if (!in) return fail(ATON_ERR_BADARG, "in is NULL");
+  if (!h->fields_set) return fail(ATON_ERR_STATE, "aton_set_fields has not been called");
+  double cur[ATON_BUDGET_LEN];
+  if (int rc = aton_photon_budget(h, cur)) return rc;
+  for (int i = 0; i < ATON_BUDGET_LEN; ++i)
+    if (i != ATON_B_STORED) h->offs[i] += in[i] - cur[i];
+  return ATON_OK;
+}
+
+int aton_get_diag(aton_handle h, aton_diag* out) {
+  if (int rc = check_h(h)) return rc;
+  if (!out) return fail(ATON_ERR_BADARG, "out is NULL");
+  if (!h->fields_set) return fail(ATON_ERR_STATE, "aton_set_fields has not been called");
+  double acc[3];
+  unsigned long long u[4];
+  if (int rc = read_tallies(h, acc, u, nullptr)) return rc;
+  out->steps = h->steps;
+  out->substeps_total = (int64_t)u[0];
+  out->substeps_max = (int64_t)u[1];
+  out->error_cells = (int64_t)u[2];
+  out->nonfinite_cells = (int64_t)u[3];
+  return ATON_OK;
+}
+
+int aton_last_error_cells(aton_handle h, int64_t* count) {
+  if (int rc = check_h(h)) return rc;
+  if (!count) return fail(ATON_ERR_BADARG, "count is NULL");
+  aton_diag d;
+  if (int rc = aton_get_diag(h, &d)) return rc;
+  *count = d.error_cells + d.nonfinite_cells;
+  return ATON_OK;
+}
+
+int aton_launches_per_step(aton_handle h, int* launches) {
+  if (int rc = check_h(h)) return rc;
+  if (!launches) return fail(ATON_ERR_BADARG, "launches is NULL");
+  if (h->mode == ATON_MODE_FUSED) *launches = 1;
+  else *launches = h->src_n > 0 ? plain_launches() : plain_launches() - 1;
+  return ATON_OK;
+}
+
+int aton_autotune(aton_handle h, int steps, int* ty_out, int* tz_out, float* ms_out) {
+  if (int rc = check_h(h)) return rc;
+  if (steps < 1) return fail(ATON_ERR_BADARG, "steps must be >= 1");
+  if (!h->fields_set) return fail(ATON_ERR_STATE, "aton_set_fields has not been called");
+  cudaStream_t s = h->stream();
+  if (int rc = fold_slots(h)) return rc;
+  // room for the finest candidate tiling, so trial steps never fold into the real tallies
+  if (int rc = ensure_slots_n(h, std::max(fused_tiles(h->nx, h->ny, h->nz, 4, std::min(16, h->nz)),
+                                          kPlainBlocks)))
+    return rc;
+  const size_t fb = sizeof(float) * (size_t)h->ncell;
+  // save the state the candidates start from
+  std::vector<float*> save(6, nullptr);
+  float* src[6] = {h->f[h->cur][0], h->f[h->cur][1], h->f[h->cur][2], h->f[h->cur][3], h->y, h->T};
+  for (int q = 0; q < 6; ++q) {
+    if (cudaMalloc(&save[q], fb) != cudaSuccess) {
+      for (auto p : save) cudaFree(p);
+      return fail(ATON_ERR_NOMEM, "autotune scratch allocation failed");
+    }
+    CU(cudaMemcpyAsync(save[q], src[q], fb, cudaMemcpyDeviceToDevice, s));
+  }
+  const int mode0 = h->mode, gb0 = h->graph_batch, ty0 = h->ty, tz0 = h->tz, cur0 = h->cur;
+  h->mode = ATON_MODE_FUSED;
+  h->graph_batch = 0;
+  int best_ty = ty0, best_tz = tz0;
+  float best = 1e30f;
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  const int tys[3] = {4, 8, 16};
+  const int tzs[5] = {16, 32, 64, 128, 256};
+  int rc = ATON_OK;
+  for (int a = 0; a < 3 && rc == ATON_OK; ++a)
+    for (int b = 0; b < 5 && rc == ATON_OK; ++b) {
+      const int tz = std::min(tzs[b], h->nz);
+      if (b > 0 && tz == std::min(tzs[b - 1], h->nz)) continue;
+      h->ty = tys[a];
+      h->tz = tz;
+      h->tiles_dirty = true;
+      if ((rc = prepare(h))) break;
+      for (int q = 0; q < 6; ++q) {
+        float* dst = q < 4 ? h->f[cur0][q] : (q == 4 ? h->y : h->T);
+        cudaMemcpyAsync(dst, save[q], fb, cudaMemcpyDeviceToDevice, s);
+      }
+      h->cur = cur0;
+      if ((rc = enqueue_step(h, s))) break;  // warm-up
+      cudaEventRecord(e0, s);
+      for (int i = 0; i < steps && rc == ATON_OK; ++i) rc = enqueue_step(h, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(ATON_ERR_CUDA, "autotune sync"); break; }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= steps;
+      if (ms < best) { best = ms; best_ty = h->ty; best_tz = h->tz; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // restore the state, drop the tallies of the trial steps
+  for (int q = 0; q < 6; ++q) {
+    float* dst = q < 4 ? h->f[cur0][q] : (q == 4 ? h->y : h->T);
+    cudaMemcpyAsync(dst, save[q], fb, cudaMemcpyDeviceToDevice, s);
+  }
+  cudaStreamSynchronize(s);
+  for (auto p : save) cudaFree(p);
+  h->cur = cur0;
+  if (h->slots.n) {
+    cudaStream_t st = s;
+    CU(cudaMemsetAsync(h->slots.acc, 0, sizeof(double) * 3 * h->slots.n, st));
+    CU(cudaMemsetAsync(h->slots.sub, 0, sizeof(unsigned long long) * h->slots.n, st));
+    CU(cudaMemsetAsync(h->slots.mx, 0, sizeof(unsigned int) * h->slots.n, st));
+    CU(cudaMemsetAsync(h->slots.err, 0, sizeof(unsigned int) * h->slots.n, st));
+    CU(cudaMemsetAsync(h->slots.nan, 0, sizeof(unsigned int) * h->slots.n, st));
+  }
+  h->mode = mode0;
+  h->graph_batch = gb0;
+  h->ty = best_ty;
+  h->tz = best_tz;
+  h->tiles_dirty = true;
+  drop_graphs(h);
+  if (rc) return rc;
+  if (ty_out) *ty_out = best_ty;
+  if (tz_out) *tz_out = best_tz;
+  if (ms_out) *ms_out = best;
+  return ATON_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,210 @@
+// aton_device.cuh -- FP32 device arithmetic of one ATON step: the M1 closure, the rate fits
+// and the sub-cycled chemistry/cooling/absorption operator of one cell.
+//
+// Device memory holds the physical flux F; the kernels scale it to Fh = F / c in registers so
+// that N and Fh share units and the transport needs the single constant lambda = c dt / dx.
+// Per-atom energies are carried in kelvin (energy / kB) so every quantity stays well inside
+// the FP32 range for nH from 1e-9 to 1e3.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace aton {
+
+// Parameters of one step, passed by value to the kernels.
+struct StepParams {
+  int nx, ny, nz;
+  int bc;              // 0 periodic, 1 transmissive
+  float lam;           // c dt / dx
+  float c, rc;         // speed of light and its reciprocal (F <-> Fh in registers)
+  float dt;            // radiative step [s]
+  float csig;          // c sigma_n [cm^3 s^-1]
+  float eheat_K;       // heat per photo-ionisation / kB [K]
+  int fixed_T, coll_ion, cooling, max_sub;
+  float T_floor, sub_eps, y_floor;
+  float clR_A, clR_b, clI_A, clI_b;
+};
+
+// ---------------------------------------------------------------------------------------
+// M1 closure (section 2.2, Eqs. 5-6, chi from f = |F|/(cN) between 1/3 and 1; Levermore
+// chi = (3 + 4f^2) / (5 + 2 s), s = sqrt(4 - 3 f^2); Eddington tensor read with the
+// coefficients swapped relative to the printed Eq. 6 so that D = I/3 at chi = 1/3).
+// Written without cancellation for small f: with g = Fh / N,
+//   N D = N [ (1 - chi)/2 I + c2 g (x) g ],   (1 - chi)/2 = (1 + s - 2 f^2) / (5 + 2 s),
+//   c2 = (3 chi - 1) / (2 f^2) = 3 (2 + 1/(2 + s)) / (5 + 2 s),
+// which follows from 4 - 2 s = 6 f^2 / (2 + s).
+// ---------------------------------------------------------------------------------------
+struct ND6 {
+  float xx, yy, zz, xy, xz, yz;
+};
+
+__device__ __forceinline__ ND6 m1_pressure(float N, float fx, float fy, float fz) {
+  ND6 r;
+  if (N > 0.f) {
+    const float rN = 1.f / N;
+    const float gx = fx * rN, gy = fy * rN, gz = fz * rN;
+    const float f2 = fminf(gx * gx + gy * gy + gz * gz, 1.f);
+    const float s = sqrtf(4.f - 3.f * f2);
+    const float r5 = 1.f / (5.f + 2.f * s);
+    const float iso = (1.f + s - 2.f * f2) * r5 * N;
+    const float c2 = 3.f * (2.f + 1.f / (2.f + s)) * r5;
+    const float cgx = c2 * fx, cgy = c2 * fy;      // c2 * g_i * N
+    r.xx = iso + cgx * gx;
+    r.yy = iso + cgy * gy;
+    r.zz = iso + c2 * fz * gz;
+    r.xy = cgx * gy;
+    r.xz = cgx * gz;
+    r.yz = cgy * gz;
+  } else {
+    r.xx = r.yy = r.zz = r.xy = r.xz = r.yz = 0.f;
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------------------------------
+// Rate fits (the paper defers to Anninos et al. 1997 and Cen 1992; section 2.2). Hui & Gnedin
+// (1997) fits in lambda = 2 T_HI / T, evaluated in log2 form, plus Cen (1992) collisional
+// excitation and bremsstrahlung. Cooling coefficients are returned divided by kB.
+// ---------------------------------------------------------------------------------------
+constexpr float kLog2TwoTHI = 18.267801676f;   // log2(2 * 157807 K)
+constexpr float kLog2e = 1.442695041f;
+constexpr float kLog10of2 = 0.301029996f;
+constexpr float kTHI = 157807.f;
+constexpr double kKB = 1.380649e-16;           // erg / K
+
+// case-B recombination rate [cm^3 s^-1]; l = log2(lambda)
+__device__ __forceinline__ float alpha_B(float l) {
+  const float q = exp2f(0.407f * (l - 1.454175893f));              // (lambda / 2.740)^0.407
+  return 2.753e-14f * exp2f(1.5f * l - 2.242f * log2f(1.f + q));
+}
+
+// collisional ionisation rate of HI [cm^3 s^-1]; l = log2(lambda), l2T = log2(T), rT = 1/T
+__device__ __forceinline__ float beta_coll(float l, float l2T, float rT) {
+  const float q = exp2f(0.874f * (l + 1.498178735f));              // (lambda / 0.354)^0.874
+  return 21.11f * exp2f(-1.5f * l2T - (kTHI * kLog2e) * rT - 1.089f * l - 1.101f * log2f(1.f + q));
+}
+
+// net cooling per H atom / kB [K s^-1] at (T, x, y = 1 - x, nH), with recombination clumping CR
+__device__ __forceinline__ float cooling_K(float T, float l, float l2T, float rT, float x, float y,
+                                           float n, float CR, bool coll_ion) {
+  // case-B recombination cooling (Hui & Gnedin 1997), times n_e n_HII
+  const float qr = exp2f(0.376f * (l - 1.169925001f));
+  const float rec = (float)(3.435e-30 / kKB) * T * exp2f(1.970f * l - 3.720f * log2f(1.f + qr));
+  // collisional excitation (Cen 1992), times n_e n_HI
+  const float ce = (float)(7.5e-19 / kKB) * exp2f(-(118348.f * kLog2e) * rT) /
+                   (1.f + sqrtf(T * 1e-5f));
+  // bremsstrahlung with the Cen (1992) Gaunt factor, times n_e n_HII
+  const float d = l2T * kLog10of2 - 5.5f;
+  const float gff = 1.1f + 0.34f * exp2f(-(kLog2e / 3.f) * d * d);
+  const float ff = (float)(1.42e-27 / kKB) * gff * sqrtf(T);
+  float lx2 = CR * rec + ff;
+  float lxy = ce;
+  if (coll_ion) lxy += kTHI * beta_coll(l, l2T, rT);   // 13.6 eV per collisional ionisation
+  return n * x * (x * lx2 + y * lxy);
+}
+
+// ---------------------------------------------------------------------------------------
+// Chemistry, photo-heating, cooling and absorption of one cell over dt: the operator Phi of
+// Appendix Eq. A4, sub-cycled (section 2.2, chemistry paragraph) with backward-difference
+// creation/destruction updates in the spirit of Anninos et al. (1997), for the balance of
+// section 3.2.1 Eq. 14 in y = 1 - x:
+//   y' - y = h [CR alpha nH x'^2 - CI c sigma_n N' y' - beta nH x y'],
+//   N' = N / (1 + nH k y'),  k = CI c sigma_n h   (photons removed = photo-ionisations).
+// g(y') = y' - y - a (1-y')^2 + k N y'/(1 + m y') + b y' is concave and increasing on [0,1]
+// with g(0) <= 0 <= g(1); Newton from y converges monotonically after at most one step.
+// Energy per atom / kB: e = 1.5 (1+x) T; e' = e + (N - N')/nH * eheat_K - h L(T) T'/T.
+// The sub-step is the largest h <= remaining with |dy/dt| h <= eps max(y, y_floor) and
+// |dT/dt| h <= eps T at the start of the sub-step; the remaining time is tracked so that
+// the last sub-step ends exactly at dt.
+// ---------------------------------------------------------------------------------------
+struct ChemOut {
+  int nsub;
+  int err;
+};
+
+__device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float& N, float& fx,
+                                             float& fy, float& fz, float& y, float& T) {
+  float CR = 1.f, CI = 1.f;
+  if (P.clR_A > 0.f) CR = fmaxf(1.f, P.clR_A * exp2f(P.clR_b * log2f(n)));
+  if (P.clI_A > 0.f) CI = fmaxf(1.f, P.clI_A * exp2f(P.clI_b * log2f(n)));
+  const float ksig = CI * P.csig;
+  float rem = P.dt;
+  float Nc = N, Tc = T, yc = fminf(fmaxf(y, 0.f), 1.f);
+  float ftot = 1.f;
+  ChemOut o{0, 0};
+  while (rem > 0.f) {
+    if (o.nsub >= P.max_sub) {
+      o.err = 1;
+      break;
+    }
+    const float xi = 1.f - yc;
+    const float l2T = log2f(Tc);
+    const float rT = 1.f / Tc;
+    const float l = kLog2TwoTHI - l2T;
+    const float alpha = CR * alpha_B(l);
+    const float beta = P.coll_ion ? beta_coll(l, l2T, rT) : 0.f;
+    const float Gam = ksig * Nc;
+    const float dydt = alpha * n * xi * xi - (Gam + beta * n * xi) * yc;
+    float h = rem;
+    const float ymax = fmaxf(yc, P.y_floor);
+    const float ady = fabsf(dydt);
+    if (ady * h > P.sub_eps * ymax) h = P.sub_eps * ymax / ady;
+    float LK = 0.f;
+    if (!P.fixed_T) {
+      if (P.cooling) LK = cooling_K(Tc, l, l2T, rT, xi, yc, n, CR, P.coll_ion != 0);
+      const float dTdt = (Gam * yc * P.eheat_K - LK) / (1.5f * (1.f + xi));
+      const float adT = fabsf(dTdt);
+      if (adT * h > P.sub_eps * Tc) h = P.sub_eps * Tc / adT;
+    }
+    const float a = h * alpha * n;
+    const float b = h * beta * n * xi;
+    const float kk = ksig * h;
+    const float m = n * kk;
+    const float kN = kk * Nc;
+    float Y = yc;
+    for (int it = 0; it < 40; ++it) {
+      const float rd = 1.f / (1.f + m * Y);
+      const float omY = 1.f - Y;
+      const float kNr = kN * rd;
+      const float g = Y - yc - a * omY * omY + kNr * Y + b * Y;
+      const float gp = 1.f + 2.f * a * omY + kNr * rd + b;
+      float Yn = fminf(fmaxf(Y - g / gp, 0.f), 1.f);
+      const float dY = fabsf(Yn - Y);
+      Y = Yn;
+      if (dY <= 3e-7f * Y) break;
+    }
+    const float fac = 1.f / (1.f + m * Y);
+    const float Nn = Nc * fac;
+    if (!P.fixed_T) {
+      const float num = 1.5f * (1.f + xi) * Tc + ((Nc - Nn) / n) * P.eheat_K;
+      const float den = 1.5f * (2.f - Y) + h * LK * rT;
+      Tc = fmaxf(num / den, P.T_floor);
+    }
+    Nc = Nn;
+    ftot *= fac;
+    yc = Y;
+    rem = (h >= rem) ? 0.f : rem - h;
+    ++o.nsub;
+  }
+  N = Nc;
+  fx *= ftot;
+  fy *= ftot;
+  fz *= ftot;
+  y = yc;
+  T = Tc;
+  return o;
+}
+
+// Kahan-compensated FP32 accumulator (per-thread tallies before the FP64 block reduction).
+struct KahanF {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float yv = v - c;
+    const float t = s + yv;
+    c = (t - s) - yv;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+}  // namespace aton

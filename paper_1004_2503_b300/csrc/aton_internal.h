@@ -1,0 +1,85 @@
+// aton_internal.h -- shared declarations of the libaton.so host code and kernels (not part
+// of the public C ABI, which is include/aton.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <utility>
+#include <vector>
+
+#include "aton.h"
+#include "aton_device.cuh"
+
+namespace aton {
+
+constexpr int kTileX = 32;          // cells per CTA row in x (one warp)
+constexpr int kPlainBlocks = 148 * 8;  // fixed grid of the unfused kernels (deterministic slots)
+constexpr int kPlainThreads = 256;
+
+// One point source of a fused tile: plane z, cell (tx + 32*ty) inside the tile, dN added.
+struct TileSrc {
+  int z;
+  int cell;
+  float dN;
+  int pad;
+};
+
+// Per-slot tallies written by the kernels (one slot per fused tile or unfused block).
+struct Slots {
+  double* acc = nullptr;              // [n][3]: absorbed, escaped, clipped (density units)
+  unsigned long long* sub = nullptr;  // [n]: sub-steps
+  unsigned int* mx = nullptr;         // [n]: max sub-steps of a cell
+  unsigned int* err = nullptr;        // [n]: cells at the sub-cycle cap
+  unsigned int* nan = nullptr;        // [n]: non-finite cells
+  int n = 0;
+};
+
+struct Fields {
+  float* N;
+  float* Fx;
+  float* Fy;
+  float* Fz;
+};
+
+struct FusedArgs {
+  StepParams P;
+  Fields in, out;
+  float* y;
+  float* T;
+  const float* nH;
+  const int* tsrc_start;  // [ntile + 1]
+  const TileSrc* tsrc;
+  Slots slots;
+  int tz;
+};
+
+struct PlainArgs {
+  StepParams P;
+  Fields in, out;
+  float* y;
+  float* T;
+  const float* nH;
+  const int* src_idx;   // merged sources
+  const float* src_dN;
+  int nsrc;
+  Slots slots;
+};
+
+// ---- launchers (aton_kernels.cu) ----
+cudaError_t init_kernel_attributes();
+cudaError_t launch_fused(int ty, const FusedArgs& a, cudaStream_t s);
+int fused_tiles(int nx, int ny, int nz, int ty, int tz);
+cudaError_t launch_plain_step(const PlainArgs& a, cudaStream_t s);
+int plain_launches();
+cudaError_t launch_scale(float* dst, const float* src, float k, int64_t n, cudaStream_t s);
+cudaError_t launch_one_minus(float* dst, const float* src, int64_t n, cudaStream_t s);
+cudaError_t launch_validate(const float* N, const float* y, const float* T, const float* nH,
+                            int64_t n, unsigned int* bad, cudaStream_t s);
+cudaError_t launch_reduce_slots(const Slots& sl, double* out_acc3, unsigned long long* out_u64_4,
+                                cudaStream_t s);
+cudaError_t launch_sum_field(const float* f, int64_t n, double* partial, double* out,
+                             cudaStream_t s);
+constexpr int kSumBlocks = 148 * 4;
+
+}  // namespace aton

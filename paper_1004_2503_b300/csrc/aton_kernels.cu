@@ -1,0 +1,548 @@
+// aton_kernels.cu -- sm_103a kernels of one ATON radiative step.
+//
+// Device memory holds the physical flux F; every load scales it to Fh = F/c and every store
+// back to F, so a saved state reloads bit for bit.
+//
+// Fused path (one kernel per step): each CTA owns a 32 x TY column tile of the grid and a
+// z-slab of tz planes, and marches through the slab plane by plane. The (N, Fh) plane with a
+// one-cell halo and the M1 pressure N D of each of its cells (computed once per cell) sit in
+// a three-deep shared-memory ring; the z neighbours of the own column stay in registers. For
+// every cell of a plane the kernel then does the Lax-Friedrichs transport (section 2.2;
+// Appendix Eqs. A2, A5), the realisability clamp, the point-source injection (section 2.3)
+// and the chemistry/cooling/absorption operator Phi (Appendix Eq. A4), and stores N, Fh, y,
+// T once. Loads of plane z+2 are issued before plane z is computed.
+//
+// Plain path (three kernels per step): transport to the other buffer, source scatter,
+// chemistry in place; the comparison baseline.
+//
+// Tallies (absorbed, escaped, clipped photons in density units; sub-step counts; error
+// counts) are reduced per CTA in FP64 and added to a per-tile slot, so sums are deterministic.
+#include "aton_internal.h"
+
+namespace aton {
+
+__device__ __forceinline__ int bc_map(int v, int n, bool periodic) {
+  if (periodic) {
+    v %= n;
+    return v < 0 ? v + n : v;
+  }
+  return v < 0 ? 0 : (v >= n ? n - 1 : v);
+}
+
+// Per-thread tallies of one step.
+struct Tally {
+  KahanF absorbed, escaped;
+  float clipped = 0.f;
+  unsigned int sub = 0, mx = 0, err = 0, nan = 0;
+};
+
+// Block reduction of the tallies (FP64 for the photon sums) into slot `slot`.
+template <int NWARP>
+__device__ __forceinline__ void flush_tally(const Tally& t, const Slots& S, int slot) {
+  __shared__ double s_acc[NWARP][3];
+  __shared__ unsigned long long s_sub[NWARP];
+  __shared__ unsigned int s_u[NWARP][3];
+  double a0 = t.absorbed.value(), a1 = t.escaped.value(), a2 = (double)t.clipped;
+  unsigned long long sb = t.sub;
+  unsigned int mx = t.mx, er = t.err, na = t.nan;
+  const unsigned full = 0xffffffffu;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 += __shfl_down_sync(full, a0, o);
+    a1 += __shfl_down_sync(full, a1, o);
+    a2 += __shfl_down_sync(full, a2, o);
+    sb += __shfl_down_sync(full, sb, o);
+    mx = max(mx, __shfl_down_sync(full, mx, o));
+    er += __shfl_down_sync(full, er, o);
+    na += __shfl_down_sync(full, na, o);
+  }
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int w = tid >> 5, lane = tid & 31;
+  if (lane == 0) {
+    s_acc[w][0] = a0; s_acc[w][1] = a1; s_acc[w][2] = a2;
+    s_sub[w] = sb; s_u[w][0] = mx; s_u[w][1] = er; s_u[w][2] = na;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double b0 = 0, b1 = 0, b2 = 0;
+    unsigned long long bs = 0;
+    unsigned int bm = 0, be = 0, bn = 0;
+    for (int i = 0; i < NWARP; ++i) {
+      b0 += s_acc[i][0]; b1 += s_acc[i][1]; b2 += s_acc[i][2];
+      bs += s_sub[i]; bm = max(bm, s_u[i][0]); be += s_u[i][1]; bn += s_u[i][2];
+    }
+    S.acc[3 * slot + 0] += b0;
+    S.acc[3 * slot + 1] += b1;
+    S.acc[3 * slot + 2] += b2;
+    S.sub[slot] += bs;
+    S.mx[slot] = max(S.mx[slot], bm);
+    S.err[slot] += be;
+    S.nan[slot] += bn;
+  }
+}
+
+// Realisability after transport: N >= 0 (the removed amount is tallied), |Fh| <= N.
+__device__ __forceinline__ void clamp_state(float& N, float& X, float& Y, float& Z, float& clipped) {
+  if (N < 0.f) {
+    clipped += N;
+    N = 0.f; X = 0.f; Y = 0.f; Z = 0.f;
+  } else {
+    const float F2 = X * X + Y * Y + Z * Z;
+    if (F2 > N * N) {
+      const float s = N * rsqrtf(F2);
+      X *= s; Y *= s; Z *= s;
+    }
+  }
+}
+
+// =========================================================================================
+// Fused step kernel
+// =========================================================================================
+template <int TY, bool PER>
+__global__ void __launch_bounds__(kTileX * TY) k_fused(const FusedArgs A) {
+  constexpr int TX = kTileX, PX = TX + 2, PL = PX * (TY + 2), NQ = 10;
+  constexpr int NH = 2 * TX + 2 * TY;
+  extern __shared__ float sm[];  // [3][NQ][PL]: N, Fx, Fy, Fz, Dxx, Dyy, Dzz, Dxy, Dxz, Dyz
+  const StepParams& P = A.P;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
+  const int nx = P.nx, ny = P.ny, nz = P.nz;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * A.tz;
+  const int z1 = min(z0 + A.tz, nz);
+  const long long plane = (long long)nx * ny;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool act = (gx < nx) && (gy < ny);
+  const long long ocol = bc_map(gx, nx, PER) + (long long)nx * bc_map(gy, ny, PER);
+  const int oslot = (ty + 1) * PX + (tx + 1);
+  int hslot = -1;
+  long long hcol = 0;
+  if (tid < NH) {
+    int hx, hy;
+    if (tid < TX) { hx = tid; hy = -1; }
+    else if (tid < 2 * TX) { hx = tid - TX; hy = TY; }
+    else if (tid < 2 * TX + TY) { hx = -1; hy = tid - 2 * TX; }
+    else { hx = TX; hy = tid - 2 * TX - TY; }
+    hslot = (hy + 1) * PX + (hx + 1);
+    hcol = bc_map(x0 + hx, nx, PER) + (long long)nx * bc_map(y0 + hy, ny, PER);
+  }
+  const float* __restrict__ iN = A.in.N;
+  const float* __restrict__ iX = A.in.Fx;
+  const float* __restrict__ iY = A.in.Fy;
+  const float* __restrict__ iZ = A.in.Fz;
+  const float rc = P.rc, cl = P.c;
+  auto pz = [&](int z) { return (long long)bc_map(z, nz, PER) * plane; };
+  auto put = [&](float* S, int slot, const float u[4], const ND6& d) {
+    S[0 * PL + slot] = u[0]; S[1 * PL + slot] = u[1];
+    S[2 * PL + slot] = u[2]; S[3 * PL + slot] = u[3];
+    S[4 * PL + slot] = d.xx; S[5 * PL + slot] = d.yy; S[6 * PL + slot] = d.zz;
+    S[7 * PL + slot] = d.xy; S[8 * PL + slot] = d.xz; S[9 * PL + slot] = d.yz;
+  };
+
+  float um[4], pm[4], uc[4], pc[4], nu[4], nh[4] = {0.f, 0.f, 0.f, 0.f};
+  // prologue: plane z0-1 (registers only) and plane z0 (ring slot 0)
+  {
+    const long long o = pz(z0 - 1) + ocol;
+    um[0] = __ldg(iN + o); um[1] = __ldg(iX + o) * rc; um[2] = __ldg(iY + o) * rc; um[3] = __ldg(iZ + o) * rc;
+    const ND6 d = m1_pressure(um[0], um[1], um[2], um[3]);
+    pm[0] = um[3]; pm[1] = d.xz; pm[2] = d.yz; pm[3] = d.zz;
+  }
+  {
+    const long long p0 = pz(z0);
+    const long long o = p0 + ocol;
+    uc[0] = __ldg(iN + o); uc[1] = __ldg(iX + o) * rc; uc[2] = __ldg(iY + o) * rc; uc[3] = __ldg(iZ + o) * rc;
+    const ND6 d = m1_pressure(uc[0], uc[1], uc[2], uc[3]);
+    pc[0] = uc[3]; pc[1] = d.xz; pc[2] = d.yz; pc[3] = d.zz;
+    put(sm, oslot, uc, d);
+    if (hslot >= 0) {
+      const long long oh = p0 + hcol;
+      float hu[4] = {__ldg(iN + oh), __ldg(iX + oh) * rc, __ldg(iY + oh) * rc, __ldg(iZ + oh) * rc};
+      put(sm, hslot, hu, m1_pressure(hu[0], hu[1], hu[2], hu[3]));
+    }
+  }
+  {
+    const long long p1 = pz(z0 + 1);
+    const long long o = p1 + ocol;
+    nu[0] = __ldg(iN + o); nu[1] = __ldg(iX + o) * rc; nu[2] = __ldg(iY + o) * rc; nu[3] = __ldg(iZ + o) * rc;
+    if (hslot >= 0) {
+      const long long oh = p1 + hcol;
+      nh[0] = __ldg(iN + oh); nh[1] = __ldg(iX + oh) * rc; nh[2] = __ldg(iY + oh) * rc; nh[3] = __ldg(iZ + oh) * rc;
+    }
+  }
+  float cy = 0.f, cT = 1.f, cn = 1.f;
+  if (act) {
+    const long long o = (long long)z0 * plane + ocol;
+    cy = A.y[o]; cT = A.T[o]; cn = __ldg(A.nH + o);
+  }
+
+  const int tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  int sp = A.tsrc_start[tile];
+  const int se = A.tsrc_start[tile + 1];
+  Tally tl;
+  const float lam = P.lam;
+
+  for (int z = z0; z < z1; ++z) {
+    const int bc = (z - z0) % 3, bn = (z - z0 + 1) % 3;
+    float* Sn = sm + bn * NQ * PL;
+    // plane z+1 into the ring (own cell and halo cell), z-flux of the own cell kept
+    float up[4] = {nu[0], nu[1], nu[2], nu[3]}, pp[4];
+    {
+      const ND6 d = m1_pressure(up[0], up[1], up[2], up[3]);
+      pp[0] = up[3]; pp[1] = d.xz; pp[2] = d.yz; pp[3] = d.zz;
+      put(Sn, oslot, up, d);
+      if (hslot >= 0) put(Sn, hslot, nh, m1_pressure(nh[0], nh[1], nh[2], nh[3]));
+    }
+    // prefetch plane z+2 and the chemistry fields of plane z+1
+    float ny_ = 0.f, nT_ = 1.f, nn_ = 1.f;
+    if (z + 1 < z1) {
+      const long long p2 = pz(z + 2);
+      const long long o = p2 + ocol;
+      nu[0] = __ldg(iN + o); nu[1] = __ldg(iX + o) * rc; nu[2] = __ldg(iY + o) * rc; nu[3] = __ldg(iZ + o) * rc;
+      if (hslot >= 0) {
+        const long long oh = p2 + hcol;
+        nh[0] = __ldg(iN + oh); nh[1] = __ldg(iX + oh) * rc; nh[2] = __ldg(iY + oh) * rc; nh[3] = __ldg(iZ + oh) * rc;
+      }
+      if (act) {
+        const long long oc = (long long)(z + 1) * plane + ocol;
+        ny_ = A.y[oc]; nT_ = A.T[oc]; nn_ = __ldg(A.nH + oc);
+      }
+    }
+    __syncthreads();
+    if (act) {
+      const float* S = sm + bc * NQ * PL;
+      const float* L = S + oslot - 1;
+      const float* R = S + oslot + 1;
+      const float* D = S + oslot - PX;
+      const float* U = S + oslot + PX;
+      const float c0 = 2.f * uc[0], c1 = 2.f * uc[1], c2 = 2.f * uc[2], c3 = 2.f * uc[3];
+      // x faces: flux (Fx, Dxx, Dxy, Dxz)
+      float aN = 0.5f * (R[1 * PL] - L[1 * PL]) - 0.5f * (R[0] - c0 + L[0]);
+      float aX = 0.5f * (R[4 * PL] - L[4 * PL]) - 0.5f * (R[1 * PL] - c1 + L[1 * PL]);
+      float aY = 0.5f * (R[7 * PL] - L[7 * PL]) - 0.5f * (R[2 * PL] - c2 + L[2 * PL]);
+      float aZ = 0.5f * (R[8 * PL] - L[8 * PL]) - 0.5f * (R[3 * PL] - c3 + L[3 * PL]);
+      // y faces: flux (Fy, Dxy, Dyy, Dyz)
+      aN += 0.5f * (U[2 * PL] - D[2 * PL]) - 0.5f * (U[0] - c0 + D[0]);
+      aX += 0.5f * (U[7 * PL] - D[7 * PL]) - 0.5f * (U[1 * PL] - c1 + D[1 * PL]);
+      aY += 0.5f * (U[5 * PL] - D[5 * PL]) - 0.5f * (U[2 * PL] - c2 + D[2 * PL]);
+      aZ += 0.5f * (U[9 * PL] - D[9 * PL]) - 0.5f * (U[3 * PL] - c3 + D[3 * PL]);
+      // z faces: flux (Fz, Dxz, Dyz, Dzz) from registers
+      aN += 0.5f * (pp[0] - pm[0]) - 0.5f * (up[0] - c0 + um[0]);
+      aX += 0.5f * (pp[1] - pm[1]) - 0.5f * (up[1] - c1 + um[1]);
+      aY += 0.5f * (pp[2] - pm[2]) - 0.5f * (up[2] - c2 + um[2]);
+      aZ += 0.5f * (pp[3] - pm[3]) - 0.5f * (up[3] - c3 + um[3]);
+      float Nn = uc[0] - lam * aN;
+      float Xn = uc[1] - lam * aX;
+      float Yn = uc[2] - lam * aY;
+      float Zn = uc[3] - lam * aZ;
+      if (!PER) {  // transmissive faces: outward photon flux through the boundary
+        float e = 0.f;
+        if (gx == 0) e -= uc[1];
+        if (gx == nx - 1) e += uc[1];
+        if (gy == 0) e -= uc[2];
+        if (gy == ny - 1) e += uc[2];
+        if (z == 0) e -= uc[3];
+        if (z == nz - 1) e += uc[3];
+        if (e != 0.f) tl.escaped.add(lam * e);
+      }
+      clamp_state(Nn, Xn, Yn, Zn, tl.clipped);
+      // point sources of this plane (host-merged: at most one entry per cell)
+      while (sp < se) {
+        const TileSrc s = A.tsrc[sp];
+        if (s.z != z) break;
+        if (s.cell == tid) Nn += s.dN;
+        ++sp;
+      }
+      const float N0 = Nn;
+      const ChemOut co = chem_cell(P, cn, Nn, Xn, Yn, Zn, cy, cT);
+      tl.absorbed.add(N0 - Nn);
+      tl.sub += co.nsub;
+      tl.mx = max(tl.mx, (unsigned)co.nsub);
+      tl.err += co.err;
+      if (!isfinite(Nn) || !isfinite(cT) || !isfinite(Xn + Yn + Zn)) tl.nan += 1;
+      const long long o = (long long)z * plane + ocol;
+      A.out.N[o] = Nn; A.out.Fx[o] = Xn * cl; A.out.Fy[o] = Yn * cl; A.out.Fz[o] = Zn * cl;
+      A.y[o] = cy; A.T[o] = cT;
+    }
+    // rotate the register window
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { um[q] = uc[q]; pm[q] = pc[q]; uc[q] = up[q]; pc[q] = pp[q]; }
+    cy = ny_; cT = nT_; cn = nn_;
+  }
+  flush_tally<TY>(tl, A.slots, tile);
+}
+
+int fused_tiles(int nx, int ny, int nz, int ty, int tz) {
+  return ((nx + kTileX - 1) / kTileX) * ((ny + ty - 1) / ty) * ((nz + tz - 1) / tz);
+}
+
+template <int TY>
+static constexpr size_t fused_smem() {
+  return sizeof(float) * 3 * 10 * (kTileX + 2) * (TY + 2);
+}
+
+template <int TY, bool PER>
+static cudaError_t set_fused_attr() {
+  return cudaFuncSetAttribute(k_fused<TY, PER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)fused_smem<TY>());
+}
+
+cudaError_t init_kernel_attributes() {
+  cudaError_t e;
+  if ((e = set_fused_attr<4, true>()) != cudaSuccess) return e;
+  if ((e = set_fused_attr<4, false>()) != cudaSuccess) return e;
+  if ((e = set_fused_attr<8, true>()) != cudaSuccess) return e;
+  if ((e = set_fused_attr<8, false>()) != cudaSuccess) return e;
+  if ((e = set_fused_attr<16, true>()) != cudaSuccess) return e;
+  return set_fused_attr<16, false>();
+}
+
+template <int TY, bool PER>
+static cudaError_t launch_fused_t(const FusedArgs& a, cudaStream_t s) {
+  const size_t smem = fused_smem<TY>();
+  dim3 grid((a.P.nx + kTileX - 1) / kTileX, (a.P.ny + TY - 1) / TY, (a.P.nz + a.tz - 1) / a.tz);
+  dim3 block(kTileX, TY);
+  k_fused<TY, PER><<<grid, block, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fused(int ty, const FusedArgs& a, cudaStream_t s) {
+  const bool per = a.P.bc == 0;
+  switch (ty) {
+    case 4: return per ? launch_fused_t<4, true>(a, s) : launch_fused_t<4, false>(a, s);
+    case 8: return per ? launch_fused_t<8, true>(a, s) : launch_fused_t<8, false>(a, s);
+    case 16: return per ? launch_fused_t<16, true>(a, s) : launch_fused_t<16, false>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// =========================================================================================
+// Plain (unfused) step: transport kernel, source kernel, chemistry kernel
+// =========================================================================================
+__device__ __forceinline__ void load_u(const Fields& f, long long o, float rc, float u[4]) {
+  u[0] = __ldg(f.N + o); u[1] = __ldg(f.Fx + o) * rc; u[2] = __ldg(f.Fy + o) * rc;
+  u[3] = __ldg(f.Fz + o) * rc;
+}
+
+template <bool PER>
+__global__ void __launch_bounds__(kPlainThreads) k_plain_transport(const PlainArgs A) {
+  const StepParams& P = A.P;
+  const int nx = P.nx, ny = P.ny, nz = P.nz;
+  const long long ncell = (long long)nx * ny * nz;
+  Tally tl;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < ncell;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(id % nx);
+    const int j = (int)((id / nx) % ny);
+    const int k = (int)(id / ((long long)nx * ny));
+    float u[4];
+    load_u(A.in, id, P.rc, u);
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int d = 0; d < 3; ++d) {
+      int ip[3] = {i, j, k}, im[3] = {i, j, k};
+      ip[d] += 1; im[d] -= 1;
+      const int n3[3] = {nx, ny, nz};
+      ip[d] = bc_map(ip[d], n3[d], PER);
+      im[d] = bc_map(im[d], n3[d], PER);
+      const long long op = ip[0] + (long long)nx * (ip[1] + (long long)ny * ip[2]);
+      const long long om = im[0] + (long long)nx * (im[1] + (long long)ny * im[2]);
+      float a[4], b[4];
+      load_u(A.in, op, P.rc, a);
+      load_u(A.in, om, P.rc, b);
+      const ND6 da = m1_pressure(a[0], a[1], a[2], a[3]);
+      const ND6 db = m1_pressure(b[0], b[1], b[2], b[3]);
+      float fa[4], fb[4];
+      if (d == 0) {
+        fa[0] = a[1]; fa[1] = da.xx; fa[2] = da.xy; fa[3] = da.xz;
+        fb[0] = b[1]; fb[1] = db.xx; fb[2] = db.xy; fb[3] = db.xz;
+      } else if (d == 1) {
+        fa[0] = a[2]; fa[1] = da.xy; fa[2] = da.yy; fa[3] = da.yz;
+        fb[0] = b[2]; fb[1] = db.xy; fb[2] = db.yy; fb[3] = db.yz;
+      } else {
+        fa[0] = a[3]; fa[1] = da.xz; fa[2] = da.yz; fa[3] = da.zz;
+        fb[0] = b[3]; fb[1] = db.xz; fb[2] = db.yz; fb[3] = db.zz;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] += 0.5f * (fa[q] - fb[q]) - 0.5f * (a[q] - 2.f * u[q] + b[q]);
+    }
+    float Nn = u[0] - P.lam * acc[0];
+    float Xn = u[1] - P.lam * acc[1];
+    float Yn = u[2] - P.lam * acc[2];
+    float Zn = u[3] - P.lam * acc[3];
+    if (!PER) {
+      float e = 0.f;
+      if (i == 0) e -= u[1];
+      if (i == nx - 1) e += u[1];
+      if (j == 0) e -= u[2];
+      if (j == ny - 1) e += u[2];
+      if (k == 0) e -= u[3];
+      if (k == nz - 1) e += u[3];
+      if (e != 0.f) tl.escaped.add(P.lam * e);
+    }
+    clamp_state(Nn, Xn, Yn, Zn, tl.clipped);
+    A.out.N[id] = Nn; A.out.Fx[id] = Xn * P.c; A.out.Fy[id] = Yn * P.c; A.out.Fz[id] = Zn * P.c;
+  }
+  flush_tally<kPlainThreads / 32>(tl, A.slots, blockIdx.x);
+}
+
+__global__ void k_plain_sources(const PlainArgs A) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < A.nsrc) A.out.N[A.src_idx[s]] += A.src_dN[s];
+}
+
+__global__ void __launch_bounds__(kPlainThreads) k_plain_chem(const PlainArgs A) {
+  const StepParams& P = A.P;
+  const long long ncell = (long long)P.nx * P.ny * P.nz;
+  Tally tl;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < ncell;
+       id += (long long)gridDim.x * blockDim.x) {
+    float N = A.out.N[id], X = A.out.Fx[id] * P.rc, Y = A.out.Fy[id] * P.rc, Z = A.out.Fz[id] * P.rc;
+    float y = A.y[id], T = A.T[id];
+    const float n = __ldg(A.nH + id);
+    const float N0 = N;
+    const ChemOut co = chem_cell(P, n, N, X, Y, Z, y, T);
+    tl.absorbed.add(N0 - N);
+    tl.sub += co.nsub;
+    tl.mx = max(tl.mx, (unsigned)co.nsub);
+    tl.err += co.err;
+    if (!isfinite(N) || !isfinite(T) || !isfinite(X + Y + Z)) tl.nan += 1;
+    A.out.N[id] = N; A.out.Fx[id] = X * P.c; A.out.Fy[id] = Y * P.c; A.out.Fz[id] = Z * P.c;
+    A.y[id] = y; A.T[id] = T;
+  }
+  flush_tally<kPlainThreads / 32>(tl, A.slots, blockIdx.x);
+}
+
+int plain_launches() { return 3; }
+
+cudaError_t launch_plain_step(const PlainArgs& a, cudaStream_t s) {
+  if (a.P.bc == 0) k_plain_transport<true><<<kPlainBlocks, kPlainThreads, 0, s>>>(a);
+  else k_plain_transport<false><<<kPlainBlocks, kPlainThreads, 0, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (a.nsrc > 0) {
+    k_plain_sources<<<(a.nsrc + 255) / 256, 256, 0, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  k_plain_chem<<<kPlainBlocks, kPlainThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// =========================================================================================
+// Utility kernels
+// =========================================================================================
+__global__ void k_scale(float* dst, const float* src, float k, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = src[i] * k;
+}
+
+__global__ void k_one_minus(float* dst, const float* src, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = 1.f - src[i];
+}
+
+__global__ void k_validate(const float* N, const float* y, const float* T, const float* nH,
+                           long long n, unsigned int* bad) {
+  unsigned int b = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float a = N[i], yy = y[i], t = T[i], h = nH[i];
+    const bool ok = isfinite(a) && a >= 0.f && isfinite(yy) && yy >= 0.f && yy <= 1.f &&
+                    isfinite(t) && t > 0.f && isfinite(h) && h > 0.f;
+    b += ok ? 0u : 1u;
+  }
+  if (b) atomicAdd(bad, b);
+}
+
+cudaError_t launch_scale(float* dst, const float* src, float k, int64_t n, cudaStream_t s) {
+  k_scale<<<148 * 4, 256, 0, s>>>(dst, src, k, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_one_minus(float* dst, const float* src, int64_t n, cudaStream_t s) {
+  k_one_minus<<<148 * 4, 256, 0, s>>>(dst, src, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate(const float* N, const float* y, const float* T, const float* nH,
+                            int64_t n, unsigned int* bad, cudaStream_t s) {
+  k_validate<<<148 * 4, 256, 0, s>>>(N, y, T, nH, n, bad);
+  return cudaGetLastError();
+}
+
+// Fixed-order FP64 reduction of the slots: out_acc3 = sums of the three photon tallies,
+// out_u64_4 = {sum sub-steps, max sub-steps, sum error cells, sum non-finite cells}.
+__global__ void __launch_bounds__(512) k_reduce_slots(const Slots S, double* out_acc3,
+                                                      unsigned long long* out4) {
+  constexpr int NT = 512;
+  __shared__ double sa[3][NT];
+  __shared__ unsigned long long su[4][NT];
+  const int t = threadIdx.x;
+  double a0 = 0, a1 = 0, a2 = 0;
+  unsigned long long sb = 0, mx = 0, er = 0, na = 0;
+  for (int i = t; i < S.n; i += NT) {
+    a0 += S.acc[3 * i]; a1 += S.acc[3 * i + 1]; a2 += S.acc[3 * i + 2];
+    sb += S.sub[i];
+    mx = max(mx, (unsigned long long)S.mx[i]);
+    er += S.err[i]; na += S.nan[i];
+  }
+  sa[0][t] = a0; sa[1][t] = a1; sa[2][t] = a2;
+  su[0][t] = sb; su[1][t] = mx; su[2][t] = er; su[3][t] = na;
+  __syncthreads();
+  for (int w = NT / 2; w > 0; w >>= 1) {
+    if (t < w) {
+      sa[0][t] += sa[0][t + w]; sa[1][t] += sa[1][t + w]; sa[2][t] += sa[2][t + w];
+      su[0][t] += su[0][t + w]; su[1][t] = max(su[1][t], su[1][t + w]);
+      su[2][t] += su[2][t + w]; su[3][t] += su[3][t + w];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    out_acc3[0] = sa[0][0]; out_acc3[1] = sa[1][0]; out_acc3[2] = sa[2][0];
+    out4[0] = su[0][0]; out4[1] = su[1][0]; out4[2] = su[2][0]; out4[3] = su[3][0];
+  }
+}
+
+cudaError_t launch_reduce_slots(const Slots& sl, double* out_acc3, unsigned long long* out4,
+                                cudaStream_t s) {
+  k_reduce_slots<<<1, 512, 0, s>>>(sl, out_acc3, out4);
+  return cudaGetLastError();
+}
+
+// Sum of a float field in FP64, fixed order: per-block partials then one block.
+__global__ void __launch_bounds__(256) k_sum_partial(const float* f, long long n, double* part) {
+  __shared__ double s[256];
+  double a = 0;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
+    a += (double)f[i];
+  s[threadIdx.x] = a;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+__global__ void __launch_bounds__(256) k_sum_final(const double* part, int n, double* out) {
+  __shared__ double s[256];
+  double a = 0;
+  for (int i = threadIdx.x; i < n; i += 256) a += part[i];
+  s[threadIdx.x] = a;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = s[0];
+}
+
+cudaError_t launch_sum_field(const float* f, int64_t n, double* partial, double* out,
+                             cudaStream_t s) {
+  k_sum_partial<<<kSumBlocks, 256, 0, s>>>(f, n, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_sum_final<<<1, 256, 0, s>>>(partial, kSumBlocks, out);
+  return cudaGetLastError();
+}
+
+}  // namespace aton

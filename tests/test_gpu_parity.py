@@ -1,0 +1,182 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on seeded inputs.
+
+Gates (after 100 steps): |x_gpu - x_oracle| <= 1e-3; |T_gpu/T_oracle - 1| <= 1e-3;
+|N_gpu/N_oracle - 1| <= 1e-3 on cells with N > 1e-6 max N. The photon budget closes to 1e-6.
+"""
+import numpy as np
+import pytest
+
+from paper_1004_2503_b300 import aton as A
+from paper_1004_2503_b300 import workloads as W
+
+from parity_helpers import (assert_gates, budget_closure, errors, run_gpu, run_oracle)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def small():
+    # 36 x 24 x 20: two 32-wide tiles in x (ragged tail of 4), three 8-row tiles in y, one slab
+    return W.workload_small()
+
+
+@pytest.fixture(scope="module")
+def small_oracle(small):
+    st, idx, rate, run = small
+    return run_oracle(st, idx, rate, run, 100)
+
+
+@pytest.mark.parametrize("mode", [A.MODE_FUSED, A.MODE_UNFUSED])
+def test_lognormal_periodic_100_steps(small, small_oracle, mode):
+    st, idx, rate, run = small
+    f, b, d, rc = run_gpu(st, idx, rate, run, 100, mode=mode)
+    assert rc == 0
+    e = errors(f, small_oracle[0])
+    print("errors", mode, e)
+    assert_gates(e, f"mode {mode}")
+    assert abs(budget_closure(b)) <= 1e-6
+    assert d["error_cells"] == 0 and d["nonfinite_cells"] == 0
+    assert d["substeps_total"] >= 100 * st["N"].size
+    # the oracle's tallies agree with the GPU's
+    ob = small_oracle[1]
+    assert b["emitted"] == pytest.approx(ob["emitted"], rel=1e-6)
+    assert b["absorbed"] == pytest.approx(ob["absorbed"], rel=1e-3)
+
+
+@pytest.mark.parametrize("fixed_T", [0, 1])
+def test_stromgren_32_transmissive(fixed_T):
+    st, idx, rate, run = W.workload_32()
+    kw = dict(fixed_T=fixed_T, coll_ion=0 if fixed_T else 1)
+    orc, ob, _ = run_oracle(st, idx, rate, run, 100, **kw)
+    f, b, d, rc = run_gpu(st, idx, rate, run, 100, **kw)
+    assert rc == 0
+    e = errors(f, orc)
+    print("errors", kw, e)
+    assert_gates(e)
+    assert abs(budget_closure(b)) <= 1e-6
+    assert b["escaped"] == pytest.approx(ob["escaped"], rel=1e-3, abs=1e-6 * ob["emitted"])
+
+
+@pytest.mark.parametrize("shape,tile", [((40, 1, 1), (4, 7)), ((2, 3, 5), (8, 1)),
+                                        ((9, 17, 33), (4, 4)), ((3, 40, 70), (16, 2))])
+def test_ragged_and_degenerate_shapes(shape, tile):
+    st, idx, rate, run = W.workload_small(shape=shape, nsrc=2, seed_field=11, seed_src=12)
+    orc, _, _ = run_oracle(st, idx, rate, run, 30)
+    for mode in (A.MODE_FUSED, A.MODE_UNFUSED):
+        f, b, d, rc = run_gpu(st, idx, rate, run, 30, mode=mode, tile=tile)
+        assert rc == 0
+        assert_gates(errors(f, orc), (shape, tile, mode))
+        assert abs(budget_closure(b)) <= 1e-6
+
+
+def test_fused_equals_unfused_closely(small):
+    st, idx, rate, run = small
+    f1, b1, _, _ = run_gpu(st, idx, rate, run, 40, mode=A.MODE_FUSED)
+    f2, b2, _, _ = run_gpu(st, idx, rate, run, 40, mode=A.MODE_UNFUSED)
+    for k in ("N", "Fx", "Fy", "Fz", "y", "T"):
+        scale = np.abs(f2[k]).max()
+        assert np.abs(f1[k] - f2[k]).max() <= 1e-5 * scale, k
+
+
+def test_tiles_and_graphs_give_identical_fields(small):
+    st, idx, rate, run = small
+    ref, bref, _, _ = run_gpu(st, idx, rate, run, 25, graph_batch=0)
+    for tile in [(4, 1), (4, 64), (8, 5), (16, 3), (16, 64)]:
+        for gb in (0, 7, 100):
+            f, b, _, _ = run_gpu(st, idx, rate, run, 25, graph_batch=gb, tile=tile)
+            for k in ("N", "Fx", "Fy", "Fz", "y", "T"):
+                assert np.array_equal(f[k], ref[k]), (tile, gb, k)
+            assert b["absorbed"] == pytest.approx(bref["absorbed"], rel=1e-9)
+
+
+def test_deterministic(small):
+    st, idx, rate, run = small
+    f1, b1, d1, _ = run_gpu(st, idx, rate, run, 20)
+    f2, b2, d2, _ = run_gpu(st, idx, rate, run, 20)
+    for k in f1:
+        assert np.array_equal(f1[k], f2[k])
+    assert b1 == b2 and d1 == d2
+
+
+def test_checkpoint_restart_is_bitwise(small):
+    st, idx, rate, run = small
+    full, bfull, _, _ = run_gpu(st, idx, rate, run, 20)
+    a = A.from_workload(st, idx, rate, run)
+    a.step(10)
+    mid = a.get_fields()
+    bmid = a.photon_budget()
+    a.close()
+    b = A.Aton(run["nx"], run["ny"], run["nz"], run["dx"], run["c"], run["dt"])
+    b.set_params(bc=A.BC_PERIODIC, sigma_n=run["sigma_n"], sigma_e=run["sigma_e"],
+                 e_gamma_eV=run["e_gamma_eV"])
+    b.set_fields(mid["N"], mid["Fx"], mid["Fy"], mid["Fz"], mid["T"],
+                 np.ascontiguousarray(st["nH"], np.float32), y=mid["y"])
+    b.set_budget(bmid)
+    b.add_sources(idx, rate)
+    b.step(10)
+    end = b.get_fields()
+    bend = b.photon_budget()
+    b.close()
+    for k in ("N", "Fx", "Fy", "Fz", "y", "T"):
+        assert np.array_equal(end[k], full[k]), k
+    assert bend["emitted"] == pytest.approx(bfull["emitted"], rel=1e-12)
+    assert bend["absorbed"] == pytest.approx(bfull["absorbed"], rel=1e-6)
+
+
+def test_device_pointers_and_stream():
+    torch = pytest.importorskip("torch")
+    st, idx, rate, run = W.workload_small(shape=(8, 16, 32), nsrc=3)
+    host, _, _, _ = run_gpu(st, idx, rate, run, 10)
+    a = A.Aton(run["nx"], run["ny"], run["nz"], run["dx"], run["c"], run["dt"])
+    a.set_params(bc=A.BC_PERIODIC, sigma_n=run["sigma_n"], sigma_e=run["sigma_e"],
+                 e_gamma_eV=run["e_gamma_eV"])
+    s = torch.cuda.Stream()
+    a.set_stream(s)
+    dev = {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).cuda() for k, v in st.items()}
+    yd = (1 - torch.from_numpy(np.asarray(st["x"], np.float64))).float().cuda()
+    torch.cuda.synchronize()
+    a.set_fields(dev["N"], dev["Fx"], dev["Fy"], dev["Fz"], dev["T"], dev["nH"], y=yd)
+    a.add_sources(idx, rate)
+    a.step(10)
+    out = a.get_fields(device=True)
+    a.set_stream(None)
+    a.close()
+    for k in ("N", "y", "T"):
+        assert np.array_equal(out[k].cpu().numpy(), host[k]), k
+
+
+def test_error_paths():
+    st, idx, rate, run = W.workload_32()
+    a = A.Aton(run["nx"], run["ny"], run["nz"], run["dx"], run["c"], run["dt"])
+    with pytest.raises(A.AtonError) as e:
+        a.step(1)
+    assert e.value.code == A.ERR_STATE
+    with pytest.raises(A.AtonError) as e:
+        a.add_sources([32 ** 3], [1.0])
+    assert e.value.code == A.ERR_BADARG
+    with pytest.raises(A.AtonError) as e:
+        a.add_sources([0], [-1.0])
+    assert e.value.code == A.ERR_BADARG
+    bad = np.ascontiguousarray(st["N"], np.float32)
+    bad[3, 4, 5] = np.nan
+    f32 = {k: np.ascontiguousarray(v, np.float32) for k, v in st.items()}
+    with pytest.raises(A.AtonError) as e:
+        a.set_fields(bad, f32["Fx"], f32["Fy"], f32["Fz"], f32["T"], f32["nH"], x=f32["x"])
+    assert e.value.code == A.ERR_NONFINITE
+    with pytest.raises(A.AtonError) as e:
+        a.set_params(sub_eps=0.0)
+    assert e.value.code == A.ERR_BADARG
+    a.close()
+
+
+def test_subcycle_cap_is_reported():
+    st, idx, rate, run = W.workload_small()
+    a = A.from_workload(st, idx, rate, run, max_sub=2)
+    a.step(5)
+    rc = a.synchronize()
+    assert rc == A.ERR_SUBCYCLE
+    assert a.last_error_cells() > 0
+    with pytest.raises(A.AtonError) as e:
+        a.step(1)
+    assert e.value.code == A.ERR_SUBCYCLE
+    a.close()

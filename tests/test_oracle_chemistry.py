@@ -1,5 +1,5 @@
 """Pins of the oracle's chemistry/cooling/absorption operator (Appendix Eq. A4; section 2.2
-chemistry paragraph; ionisation balance of Eq. 14) and of its rate fits."""
+chemistry paragraph; ionisation balance of section 3.2.1, Eq. 14) and of its rate fits."""
 import math
 import os
 
