@@ -38,25 +38,38 @@ struct ND6 {
   float xx, yy, zz, xy, xz, yz;
 };
 
+// Below kNTiny (photons cm^-3) the cell holds no radiation worth transporting and 1/N would
+// leave the FP32 range (N reaches the denormals ahead of fronts through the scheme's
+// diffusion); there D = I/3 (f = 0) is used. Unrealisable inputs with |Fh| > N take f = 1
+// along Fh, as D = n (x) n requires.
+constexpr float kNTiny = 1e-30f;
+
 __device__ __forceinline__ ND6 m1_pressure(float N, float fx, float fy, float fz) {
   ND6 r;
-  if (N > 0.f) {
+  if (N > kNTiny) {
     const float rN = 1.f / N;
-    const float gx = fx * rN, gy = fy * rN, gz = fz * rN;
-    const float f2 = fminf(gx * gx + gy * gy + gz * gz, 1.f);
+    float gx = fx * rN, gy = fy * rN, gz = fz * rN;
+    float f2 = gx * gx + gy * gy + gz * gz;
+    if (f2 > 1.f) {
+      const float k = rsqrtf(f2);
+      gx *= k; gy *= k; gz *= k;
+      f2 = 1.f;
+    }
     const float s = sqrtf(4.f - 3.f * f2);
     const float r5 = 1.f / (5.f + 2.f * s);
     const float iso = (1.f + s - 2.f * f2) * r5 * N;
-    const float c2 = 3.f * (2.f + 1.f / (2.f + s)) * r5;
-    const float cgx = c2 * fx, cgy = c2 * fy;      // c2 * g_i * N
-    r.xx = iso + cgx * gx;
-    r.yy = iso + cgy * gy;
-    r.zz = iso + c2 * fz * gz;
-    r.xy = cgx * gy;
-    r.xz = cgx * gz;
-    r.yz = cgy * gz;
+    const float Nc2 = 3.f * (2.f + 1.f / (2.f + s)) * r5 * N;
+    const float ax = Nc2 * gx, ay = Nc2 * gy;
+    r.xx = iso + ax * gx;
+    r.yy = iso + ay * gy;
+    r.zz = iso + Nc2 * gz * gz;
+    r.xy = ax * gy;
+    r.xz = ax * gz;
+    r.yz = ay * gz;
   } else {
-    r.xx = r.yy = r.zz = r.xy = r.xz = r.yz = 0.f;
+    const float iso = N > 0.f ? N * (1.f / 3.f) : 0.f;
+    r.xx = r.yy = r.zz = iso;
+    r.xy = r.xz = r.yz = 0.f;
   }
   return r;
 }
@@ -114,8 +127,8 @@ __device__ __forceinline__ float cooling_K(float T, float l, float l2T, float rT
 // with g(0) <= 0 <= g(1); Newton from y converges monotonically after at most one step.
 // Energy per atom / kB: e = 1.5 (1+x) T; e' = e + (N - N')/nH * eheat_K - h L(T) T'/T.
 // The sub-step is the largest h <= remaining with |dy/dt| h <= eps max(y, y_floor) and
-// |dT/dt| h <= eps T at the start of the sub-step; the remaining time is tracked so that
-// the last sub-step ends exactly at dt.
+// |dT/dt| h <= eps T at the start of the sub-step (dropped for gas at the floor that would
+// cool); the remaining time is tracked so that the last sub-step ends exactly at dt.
 // ---------------------------------------------------------------------------------------
 struct ChemOut {
   int nsub;
@@ -154,7 +167,8 @@ __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float
       if (P.cooling) LK = cooling_K(Tc, l, l2T, rT, xi, yc, n, CR, P.coll_ion != 0);
       const float dTdt = (Gam * yc * P.eheat_K - LK) / (1.5f * (1.f + xi));
       const float adT = fabsf(dTdt);
-      if (adT * h > P.sub_eps * Tc) h = P.sub_eps * Tc / adT;
+      const bool pinned = Tc <= P.T_floor && dTdt < 0.f;   // cannot cool below the floor
+      if (!pinned && adT * h > P.sub_eps * Tc) h = P.sub_eps * Tc / adT;
     }
     const float a = h * alpha * n;
     const float b = h * beta * n * xi;

@@ -88,8 +88,8 @@ __device__ __forceinline__ void clamp_state(float& N, float& X, float& Y, float&
     N = 0.f; X = 0.f; Y = 0.f; Z = 0.f;
   } else {
     const float F2 = X * X + Y * Y + Z * Z;
-    if (F2 > N * N) {
-      const float s = N * rsqrtf(F2);
+    if (F2 > N * N) {   // IEEE sqrt and division: F2 may be denormal, N may be 0
+      const float s = N > 0.f ? N / sqrtf(F2) : 0.f;
       X *= s; Y *= s; Z *= s;
     }
   }

@@ -79,14 +79,25 @@ def test_fused_equals_unfused_closely(small):
 
 
 def test_tiles_and_graphs_give_identical_fields(small):
+    """Per-cell arithmetic does not depend on the slab depth or on graph batching: bitwise
+    equal for one tile height. Different tile heights are separate compiled kernels whose
+    floating-point contraction may differ by an ulp: equal to 1e-5."""
     st, idx, rate, run = small
-    ref, bref, _, _ = run_gpu(st, idx, rate, run, 25, graph_batch=0)
-    for tile in [(4, 1), (4, 64), (8, 5), (16, 3), (16, 64)]:
+    refs = {}
+    for ty in (4, 8, 16):
+        refs[ty] = run_gpu(st, idx, rate, run, 25, graph_batch=0, tile=(ty, 64))
+    for tile in [(4, 1), (8, 5), (16, 3), (8, 64)]:
         for gb in (0, 7, 100):
             f, b, _, _ = run_gpu(st, idx, rate, run, 25, graph_batch=gb, tile=tile)
+            ref, bref, _, _ = refs[tile[0]]
             for k in ("N", "Fx", "Fy", "Fz", "y", "T"):
                 assert np.array_equal(f[k], ref[k]), (tile, gb, k)
-            assert b["absorbed"] == pytest.approx(bref["absorbed"], rel=1e-9)
+            # per-thread FP32 tally partitions differ with the slab depth
+            assert b["absorbed"] == pytest.approx(bref["absorbed"], rel=1e-7)
+    for ty in (4, 16):
+        for k in ("N", "Fx", "Fy", "Fz", "y", "T"):
+            a, r = refs[ty][0][k], refs[8][0][k]
+            assert np.abs(a - r).max() <= 1e-5 * np.abs(r).max(), (ty, k)
 
 
 def test_deterministic(small):
@@ -180,3 +191,27 @@ def test_subcycle_cap_is_reported():
         a.step(1)
     assert e.value.code == A.ERR_SUBCYCLE
     a.close()
+
+
+def test_degenerate_values_stay_finite():
+    """Denormal and zero photon densities (with and without flux), fully neutral and fully
+    ionised cells and gas at the temperature floor: the step stays finite and on the oracle."""
+    st, idx, rate, run = W.workload_small(shape=(8, 12, 16), nsrc=2, seed_field=21, seed_src=22)
+    c = run["c"]
+    N = st["N"]
+    N[0, 0, :4] = 1e-40                # FP32 denormals
+    st["Fx"][0, 0, :4] = 0.5 * c * 1e-40
+    N[1, 1, 3] = 0.0
+    st["Fy"][1, 1, 3] = 1e-12          # flux with no photons (clamped away)
+    N[2, 2, 2] = 1e-3
+    st["Fz"][2, 2, 2] = 3.0 * c * 1e-3  # |F| > cN: unrealisable, treated as f = 1
+    st["x"][3, :, :] = 1.0
+    st["x"][4, :, :] = 0.0
+    st["T"][5, :, :] = 1.0
+    orc, _, _ = run_oracle(st, idx, rate, run, 8)
+    for mode in (A.MODE_FUSED, A.MODE_UNFUSED):
+        f, b, d, rc = run_gpu(st, idx, rate, run, 8, mode=mode)
+        assert rc == 0 and d["nonfinite_cells"] == 0
+        for k in ("N", "Fx", "Fy", "Fz", "y", "T"):
+            assert np.isfinite(f[k]).all(), k
+        assert_gates(errors(f, orc), mode)

@@ -184,3 +184,12 @@ def test_result_is_continuous_in_the_step_length():
     assert len(set(ns)) > 1            # the window crosses a change of sub-step count
     assert np.abs(np.diff(xs)).max() < 1e-3
     assert np.abs(np.diff(Ts) / Ts[1:]).max() < 1e-3
+
+
+def test_gas_at_the_floor_that_would_cool_takes_one_substep():
+    """T cannot fall below the floor, so the temperature condition of the sub-step rule does
+    not apply there: a cold cell with nothing to heat it finishes in one sub-step."""
+    p = O.params(dt=1e11, sigma_n=SIG, sigma_e=SIG, e_gamma_eV=29.6)
+    r = O.chem_cell(p, 1e-3, 0.0, [0, 0, 0], 1e-4, p.T_floor)
+    assert r["err"] == 0 and r["nsub"] == 1
+    assert r["T"] == pytest.approx(p.T_floor, rel=1e-6)
