@@ -225,8 +225,9 @@ void orc_transport(const orc_params* p, int nx, int ny, int nz,
  * F decays by the same factor as N. The energy E = 1.5 nH (1+x) kB T gains the photo-heating
  * of the absorbed photons and loses the cooling rate linearised in T (semi-implicit).
  * The sub-step is the largest h <= remaining time with |dy/dt| h <= eps max(y, y_floor) and
- * |dT/dt| h <= eps T, evaluated at the start of the sub-step; the temperature condition is
- * dropped for gas at the floor that would cool (T cannot fall there).
+ * (heating + cooling) h <= eps E (the heating and the cooling time each bound the step, as
+ * their difference cancels near thermal balance), evaluated at the start of the sub-step; the
+ * temperature condition is dropped for gas at the floor that would cool (T cannot fall).
  * ------------------------------------------------------------------------------------------ */
 int orc_chem_cell(const orc_params* p, double nH, double* N, double* Fx, double* Fy, double* Fz,
                   double* x, double* T, double* absorbed_per_volume, int64_t* nsub) {
@@ -257,10 +258,12 @@ int orc_chem_cell(const orc_params* p, double nH, double* N, double* Fx, double*
     if (!p->fixed_T) {
       Lam = orc_cooling_rate(p, Tc, xi, n);
       double heat_rate = n * Gam * y * eheat;                 /* erg cm^-3 s^-1 */
-      double dTdt = (heat_rate - Lam) / (1.5 * ORC_KB * n * (1.0 + xi));
+      /* gross rate of change of T: heating and cooling each bounded (heating and cooling
+       * times), not their difference, which cancels near thermal balance */
+      double rate = (heat_rate + Lam) / (1.5 * ORC_KB * n * (1.0 + xi));
       /* at the floor, cooling cannot lower T: the temperature criterion does not apply */
-      int pinned = Tc <= p->T_floor && dTdt < 0.0;
-      if (!pinned && fabs(dTdt) * h > p->sub_eps * Tc) h = p->sub_eps * Tc / fabs(dTdt);
+      int pinned = Tc <= p->T_floor && heat_rate < Lam;
+      if (!pinned && rate * h > p->sub_eps * Tc) h = p->sub_eps * Tc / rate;
     }
     /* implicit (N', y') */
     double a = h * alpha * n;

@@ -127,8 +127,8 @@ __device__ __forceinline__ float cooling_K(float T, float l, float l2T, float rT
 // with g(0) <= 0 <= g(1); Newton from y converges monotonically after at most one step.
 // Energy per atom / kB: e = 1.5 (1+x) T; e' = e + (N - N')/nH * eheat_K - h L(T) T'/T.
 // The sub-step is the largest h <= remaining with |dy/dt| h <= eps max(y, y_floor) and
-// |dT/dt| h <= eps T at the start of the sub-step (dropped for gas at the floor that would
-// cool); the remaining time is tracked so that the last sub-step ends exactly at dt.
+// (heating + cooling) h <= eps T (gross rates; dropped for gas at the floor that would cool)
+// at the start of the sub-step; the last sub-step ends exactly at dt.
 // ---------------------------------------------------------------------------------------
 struct ChemOut {
   int nsub;
@@ -141,15 +141,20 @@ __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float
   if (P.clR_A > 0.f) CR = fmaxf(1.f, P.clR_A * exp2f(P.clR_b * log2f(n)));
   if (P.clI_A > 0.f) CI = fmaxf(1.f, P.clI_A * exp2f(P.clI_b * log2f(n)));
   const float ksig = CI * P.csig;
-  float rem = P.dt;
+  // Remaining time as an unevaluated float pair rh + rl (error-free TwoSum updates): a plain
+  // FP32 "rem -= h" stalls once h < ulp(rem)/2 (about 4e3 s for dt ~ 1e11 s, while dense gas
+  // can need sub-steps of 1e3 s), and rounding h to coarse ticks would change the sequence.
+  float rh = P.dt, rl = 0.f;
+  const float N0 = N;
   float Nc = N, Tc = T, yc = fminf(fmaxf(y, 0.f), 1.f);
-  float ftot = 1.f;
+  float Nh = N, Nl = 0.f;   // N as an unevaluated pair Nh + Nl
   ChemOut o{0, 0};
-  while (rem > 0.f) {
+  while (rh > 0.f) {
     if (o.nsub >= P.max_sub) {
       o.err = 1;
       break;
     }
+    const float rem = rh;
     const float xi = 1.f - yc;
     const float l2T = log2f(Tc);
     const float rT = 1.f / Tc;
@@ -165,45 +170,79 @@ __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float
     float LK = 0.f;
     if (!P.fixed_T) {
       if (P.cooling) LK = cooling_K(Tc, l, l2T, rT, xi, yc, n, CR, P.coll_ion != 0);
-      const float dTdt = (Gam * yc * P.eheat_K - LK) / (1.5f * (1.f + xi));
-      const float adT = fabsf(dTdt);
-      const bool pinned = Tc <= P.T_floor && dTdt < 0.f;   // cannot cool below the floor
-      if (!pinned && adT * h > P.sub_eps * Tc) h = P.sub_eps * Tc / adT;
+      // gross rate: heating and cooling each bounded (no cancellation near thermal balance)
+      const float heat = Gam * yc * P.eheat_K;
+      const float rate = (heat + LK) / (1.5f * (1.f + xi));
+      const bool pinned = Tc <= P.T_floor && heat < LK;   // cannot cool below the floor
+      if (!pinned && rate * h > P.sub_eps * Tc) h = P.sub_eps * Tc / rate;
     }
+    const bool last = !(h < rem);   // the last sub-step ends exactly at dt
     const float a = h * alpha * n;
     const float b = h * beta * n * xi;
     const float kk = ksig * h;
     const float m = n * kk;
     const float kN = kk * Nc;
-    float Y = yc;
+    // Newton on the change d = y - y' (no cancellation in y' - y when the change is small):
+    // g = -d - a (x + d)^2 + kN y'/(1 + m y') + b y', dg/dd = -(1 + 2a(x+d) + kN/(1+my')^2 + b)
+    float d = 0.f;
     for (int it = 0; it < 40; ++it) {
-      const float rd = 1.f / (1.f + m * Y);
-      const float omY = 1.f - Y;
+      const float Yv = yc - d;
+      const float omY = xi + d;
+      const float rd = 1.f / (1.f + m * Yv);
       const float kNr = kN * rd;
-      const float g = Y - yc - a * omY * omY + kNr * Y + b * Y;
+      const float g = -d - a * omY * omY + kNr * Yv + b * Yv;
       const float gp = 1.f + 2.f * a * omY + kNr * rd + b;
-      float Yn = fminf(fmaxf(Y - g / gp, 0.f), 1.f);
-      const float dY = fabsf(Yn - Y);
-      Y = Yn;
-      if (dY <= 3e-7f * Y) break;
+      const float dn = fminf(fmaxf(d + g / gp, yc - 1.f), yc);
+      const float dd = fabsf(dn - d);
+      d = dn;
+      if (dd <= 3e-7f * fabsf(d)) break;
     }
-    const float fac = 1.f / (1.f + m * Y);
-    const float Nn = Nc * fac;
+    const float Y = yc - d;
+    // photons absorbed in the sub-step: N r with r = m y'/(1 + m y'). N keeps full relative
+    // precision either way: a large fraction is applied as N/(1 + m y') (no cancellation), a
+    // small one (down to r << ulp(1)) is subtracted from the pair with an error-free TwoSum.
+    const float mY = m * Y;
+    const float r = mY / (1.f + mY);
+    const float dN = Nc * r;
+    if (r > 0.5f) {
+      Nh = Nc / (1.f + mY);
+      Nl = 0.f;
+    } else {
+      const float sm = Nh - dN;
+      const float bv = sm - Nh;
+      const float er = (Nh - (sm - bv)) + (-dN - bv);
+      const float lo = Nl + er;
+      Nh = sm + lo;
+      Nl = lo - (Nh - sm);
+    }
+    Nh = fmaxf(Nh, 0.f);
+    const float Nn = Nh + Nl;
     if (!P.fixed_T) {
-      const float num = 1.5f * (1.f + xi) * Tc + ((Nc - Nn) / n) * P.eheat_K;
+      const float num = 1.5f * (1.f + xi) * Tc + (dN / n) * P.eheat_K;
       const float den = 1.5f * (2.f - Y) + h * LK * rT;
       Tc = fmaxf(num / den, P.T_floor);
     }
     Nc = Nn;
-    ftot *= fac;
     yc = Y;
-    rem = (h >= rem) ? 0.f : rem - h;
     ++o.nsub;
+    if (last) {
+      rh = 0.f;
+    } else {  // rh + rl -= h, TwoSum then renormalise
+      const float sm = rh - h;
+      const float bv = sm - rh;
+      const float er = (rh - (sm - bv)) + (-h - bv);
+      const float lo = rl + er;
+      rh = sm + lo;
+      rl = lo - (rh - sm);
+    }
   }
+  // F decays by the same factor as N in every sub-step, so by N_final / N_0 overall (after the
+  // realisability clamp N = 0 implies F = 0)
+  const float fr = N0 > 0.f ? Nc / N0 : 1.f;
   N = Nc;
-  fx *= ftot;
-  fy *= ftot;
-  fz *= ftot;
+  fx *= fr;
+  fy *= fr;
+  fz *= fr;
   y = yc;
   T = Tc;
   return o;

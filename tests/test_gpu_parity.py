@@ -215,3 +215,51 @@ def test_degenerate_values_stay_finite():
         for k in ("N", "Fx", "Fy", "Fz", "y", "T"):
             assert np.isfinite(f[k]).all(), k
         assert_gates(errors(f, orc), mode)
+
+
+def _one_cell(run, N, F, y, T, n, **kw):
+    """One step of a 1x1x1 periodic grid: transport is the identity, so this is the chemistry
+    operator of one cell through the C ABI."""
+    h = A.Aton(1, 1, 1, run["dx"], run["c"], run["dt"])
+    h.set_params(sigma_n=run["sigma_n"], sigma_e=run["sigma_e"], e_gamma_eV=run["e_gamma_eV"], **kw)
+    f = lambda v: np.array([v], np.float32)  # noqa: E731
+    h.set_fields(f(N), f(F[0]), f(F[1]), f(F[2]), f(T), f(n), y=f(y))
+    h.step(1)
+    rc = h.synchronize()
+    out = h.get_fields()
+    d = h.diag()
+    h.close()
+    return rc, {k: float(v.ravel()[0]) for k, v in out.items()}, d
+
+
+def test_chemistry_of_single_cells_matches_the_oracle():
+    """Random cell states over the ranges the workloads reach (n_H 1e-9..10 cm^-3, 0..100
+    photons per atom, neutral to fully ionised, 1 K..1e6 K), plus the dense cold cell hit by
+    40 photons per atom that needs ~100 sub-steps."""
+    import oracle as O
+    from parity_helpers import oracle_params
+    st, idx, rate, run = W.workload_small(shape=(2, 2, 2), nsrc=1)
+    p = oracle_params(run)
+    rng = np.random.default_rng(5)
+    cases = [(2.407596854603867e-05, 0.0, 0.9998999834060669, 1.0, 5.894661180401288e-07)]
+    for _ in range(150):
+        n = 10 ** rng.uniform(-9, 1)
+        N = n * 10 ** rng.uniform(-8, 2) * (rng.random() < 0.85)
+        y = 10 ** rng.uniform(-7, 0) if rng.random() < 0.5 else 1 - 10 ** rng.uniform(-6, 0)
+        T = 10 ** rng.uniform(0, 6)
+        cases.append((N, 0.3 * run["c"] * N, y, T, n))
+    worst = dict(x=0.0, T=0.0, N=0.0)
+    for N, Fx, y, T, n in cases:
+        N32, y32, T32, n32 = (float(np.float32(v)) for v in (N, y, T, n))
+        F32 = float(np.float32(Fx))
+        rc, g, d = _one_cell(run, N32, (F32, 0.0, 0.0), y32, T32, n32)
+        assert rc == 0, (N, y, T, n, d)
+        r = O.chem_cell(p, n32, N32, [F32, 0, 0], 1 - y32, T32)
+        worst["x"] = max(worst["x"], abs(g["x"] - r["x"]))
+        worst["T"] = max(worst["T"], abs(g["T"] - r["T"]) / r["T"])
+        # the remainder of a cell that absorbs nearly all its photons goes as exp(-tau):
+        # compared where more than 1e-3 of them are left
+        if r["N"] > 1e-3 * N32:
+            worst["N"] = max(worst["N"], abs(g["N"] - r["N"]) / r["N"])
+    print("single-cell worst", worst)
+    assert worst["x"] <= 1e-3 and worst["T"] <= 1e-3 and worst["N"] <= 1e-3, worst
