@@ -184,6 +184,25 @@ int aton_last_error_cells(aton_handle h, int64_t* count);
 /* Number of kernel launches per radiative step of the current execution mode. */
 int aton_launches_per_step(aton_handle h, int* launches);
 
+/* Photon count sum(N) * cell_volume [photons] of a float32 device field N of n cells, summed
+ * in FP64 in a fixed order, written to *out (host memory). The paper has no counterpart: this
+ * entry point exists for callers that cannot let a library allocate device memory (a host
+ * code that hands out all device memory from its own fixed pool, or a hook run between time
+ * steps where an allocation could block on queued work). It calls no cudaMalloc, cudaFree or
+ * other allocating routine: its scratch is a fixed file-scope device array of 16384 FP64
+ * partial sums plus a result slot (about 128 KB), held by every GPU that loads the library
+ * until the process exits, so n is limited to 16384 * 65536 = 2^30 cells (1024^3).
+ * N must be device memory of the current device; `stream` is a cudaStream_t (NULL: the
+ * legacy default stream); the call enqueues two kernels and a copy on it and waits for them.
+ * The first call on each device looks up the scratch address (cudaGetSymbolAddress with that
+ * device current); make that first call before any stream capture. All calls share the one
+ * scratch array (each call rewrites every slot it reads), so calls that overlap on the GPU
+ * (from several host threads or streams at once) race and give wrong sums.
+ * Errors: BADARG (NULL pointer, n < 1 or n > 2^30, cell_volume not positive and finite, N not
+ * device memory of the current device), CUDA. */
+int aton_photon_sum_static(const float* N, int64_t n, double cell_volume, double* out,
+                           void* stream);
+
 /* Static description of a status code. */
 const char* aton_strerror(int code);
 

@@ -28,7 +28,7 @@ EXPORTS = (
     "aton_set_stream", "aton_set_exec", "aton_set_tile", "aton_autotune", "aton_set_fields",
     "aton_get_fields", "aton_add_sources", "aton_step", "aton_synchronize",
     "aton_photon_budget", "aton_set_budget", "aton_get_diag", "aton_last_error_cells",
-    "aton_launches_per_step", "aton_strerror", "aton_last_message",
+    "aton_launches_per_step", "aton_strerror", "aton_last_message", "aton_photon_sum_static",
 )
 
 
@@ -94,6 +94,7 @@ def load():
     L.aton_launches_per_step.argtypes = [_VP, C.POINTER(C.c_int)]
     L.aton_strerror.argtypes = [C.c_int]
     L.aton_strerror.restype = C.c_char_p
+    L.aton_photon_sum_static.argtypes = [_VP, C.c_int64, C.c_double, C.POINTER(C.c_double), _VP]
     L.aton_last_message.argtypes = []
     L.aton_last_message.restype = C.c_char_p
     for name in EXPORTS:
@@ -266,6 +267,18 @@ class Aton:
         n = C.c_int()
         _check(self.L.aton_launches_per_step(self.h, C.byref(n)), "aton_launches_per_step")
         return n.value
+
+
+def photon_sum_static(N, cell_volume, stream=None):
+    """sum(N) * cell_volume of a float32 torch CUDA tensor through aton_photon_sum_static: the
+    variant that allocates no device memory (for callers that cannot let a library allocate;
+    see include/aton.h for the size limit and the shared scratch)."""
+    ptr = _ptr(N, DEVICE)
+    out = C.c_double()
+    s = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    _check(load().aton_photon_sum_static(ptr, int(N.numel()), float(cell_volume), C.byref(out), s),
+           "aton_photon_sum_static")
+    return out.value
 
 
 def from_workload(state, src_idx, src_rate, run, **params):

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libaton.so")
-SOURCES = ["aton_capi.cu", "aton_kernels.cu"]
+SOURCES = ["aton_capi.cu", "aton_kernels.cu", "aton_static.cu"]
 HEADERS = ["aton_device.cuh", "aton_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

@@ -33,6 +33,8 @@ static int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+void aton::set_last_message(const char* msg) { g_msg = msg ? msg : ""; }
+
 #define CU(call)                                                                    \
   do {                                                                              \
     cudaError_t e_ = (call);                                                        \

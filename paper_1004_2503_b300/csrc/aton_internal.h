@@ -66,6 +66,9 @@ struct PlainArgs {
   Slots slots;
 };
 
+// ---- last-failure message of the calling thread (aton_capi.cu) ----
+void set_last_message(const char* msg);
+
 // ---- launchers (aton_kernels.cu) ----
 cudaError_t init_kernel_attributes();
 cudaError_t launch_fused(int ty, const FusedArgs& a, cudaStream_t s);
