@@ -191,7 +191,12 @@ def ours(args, world, rank, local):
 
     a = A.from_workload(st, idx, rate, run)
     a.set_stream(stream)
-    ty, tz, tune_ms = a.autotune(3)
+    if args.tile:
+        ty, tz = (int(v) for v in args.tile.split(","))
+        a.set_tile(ty, tz)
+        tune_ms = None
+    else:
+        ty, tz, tune_ms = a.autotune(3)
     a.set_exec(A.MODE_FUSED, args.graph_batch)
     a.step(args.warmup)
     a.synchronize()
@@ -215,21 +220,28 @@ def ours(args, world, rank, local):
     ms = 1e3 * t / args.steps
 
     # plain unfused three-kernel step at the same accuracy, from the same state
+    unfused = None
     ku = max(3, min(args.steps, 200))
-    a.set_exec(A.MODE_UNFUSED, args.graph_batch)
-    a.step(3)
-    a.synchronize()
-    u0 = torch.cuda.Event(enable_timing=True)
-    u1 = torch.cuda.Event(enable_timing=True)
-    u0.record(stream)
-    a.step(ku)
-    u1.record(stream)
-    u1.synchronize()
-    tu = u0.elapsed_time(u1) / 1e3
-    unfused = {"value": ncell * ku / tu, "ms_per_step": 1e3 * tu / ku,
-               "launches_per_step": a.launches_per_step(), "steps": ku,
-               "achieved_gbs_at_52B": BYTES_PER_CELL * ncell * ku / tu / 1e9}
+    if args.no_unfused:
+        ku = 0
+    if ku:
+        a.set_exec(A.MODE_UNFUSED, args.graph_batch)
+        a.step(3)
+        a.synchronize()
+        u0 = torch.cuda.Event(enable_timing=True)
+        u1 = torch.cuda.Event(enable_timing=True)
+        u0.record(stream)
+        a.step(ku)
+        u1.record(stream)
+        u1.synchronize()
+        tu = u0.elapsed_time(u1) / 1e3
+        unfused = {"value": ncell * ku / tu, "ms_per_step": 1e3 * tu / ku,
+                   "launches_per_step": a.launches_per_step(), "steps": ku,
+                   "achieved_gbs_at_52B": BYTES_PER_CELL * ncell * ku / tu / 1e9}
     a.close()
+    if args.no_e2e:
+        return finish(args, world, rank, dist, st, idx, rate, run, desc, ncell, value, ms, t,
+                      ty, tz, tune_ms, unfused, None, launches, clk, rc, diag, bud)
 
     # end to end through the C ABI with host buffers (pinned): state in, every step a source
     # list in and the photon budget out, state out at the end
@@ -265,6 +277,12 @@ def ours(args, world, rank, local):
            "what": "set_fields(host, pinned) once + per step add_sources(host) + aton_step(1) "
                    "+ aton_photon_budget(host) + get_fields(host) once"}
 
+    return finish(args, world, rank, dist, st, idx, rate, run, desc, ncell, value, ms, t,
+                  ty, tz, tune_ms, unfused, e2e, launches, clk, rc, diag, bud)
+
+
+def finish(args, world, rank, dist, st, idx, rate, run, desc, ncell, value, ms, t, ty, tz,
+           tune_ms, unfused, e2e, launches, clk, rc, diag, bud):
     peak, peak_kind = peaks()
     achieved = BYTES_PER_CELL * ncell / (t / args.steps) / 1e9
     kh = kernel_hash()
@@ -315,6 +333,9 @@ def main():
     ap.add_argument("--grid", type=int, default=512)
     ap.add_argument("--graph-batch", type=int, default=100)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-unfused", action="store_true")
+    ap.add_argument("--tile", default="", help="TY,TZ of the fused kernel (skips the autotuner)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

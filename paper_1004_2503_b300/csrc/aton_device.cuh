@@ -84,6 +84,10 @@ constexpr float kLog2e = 1.442695041f;
 constexpr float kLog10of2 = 0.301029996f;
 constexpr float kTHI = 157807.f;
 constexpr double kKB = 1.380649e-16;           // erg / K
+// Below these temperatures exp(-157807/T) (collisional ionisation) and exp(-118348/T)
+// (collisional excitation) are under the smallest normal FP32 number and flush to exactly 0.
+constexpr float kTBetaMin = 1700.f;
+constexpr float kTExcMin = 1300.f;
 
 // case-B recombination rate [cm^3 s^-1]; l = log2(lambda)
 __device__ __forceinline__ float alpha_B(float l) {
@@ -103,16 +107,17 @@ __device__ __forceinline__ float cooling_K(float T, float l, float l2T, float rT
   // case-B recombination cooling (Hui & Gnedin 1997), times n_e n_HII
   const float qr = exp2f(0.376f * (l - 1.169925001f));
   const float rec = (float)(3.435e-30 / kKB) * T * exp2f(1.970f * l - 3.720f * log2f(1.f + qr));
-  // collisional excitation (Cen 1992), times n_e n_HI
-  const float ce = (float)(7.5e-19 / kKB) * exp2f(-(118348.f * kLog2e) * rT) /
-                   (1.f + sqrtf(T * 1e-5f));
+  // collisional excitation (Cen 1992), times n_e n_HI (exactly 0 in FP32 below kTExcMin)
+  const float ce = T > kTExcMin ? (float)(7.5e-19 / kKB) * exp2f(-(118348.f * kLog2e) * rT) /
+                                       (1.f + sqrtf(T * 1e-5f))
+                                 : 0.f;
   // bremsstrahlung with the Cen (1992) Gaunt factor, times n_e n_HII
   const float d = l2T * kLog10of2 - 5.5f;
   const float gff = 1.1f + 0.34f * exp2f(-(kLog2e / 3.f) * d * d);
   const float ff = (float)(1.42e-27 / kKB) * gff * sqrtf(T);
   float lx2 = CR * rec + ff;
   float lxy = ce;
-  if (coll_ion) lxy += kTHI * beta_coll(l, l2T, rT);   // 13.6 eV per collisional ionisation
+  if (coll_ion && T > kTBetaMin) lxy += kTHI * beta_coll(l, l2T, rT);   // 13.6 eV each
   return n * x * (x * lx2 + y * lxy);
 }
 
@@ -160,7 +165,8 @@ __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float
     const float rT = 1.f / Tc;
     const float l = kLog2TwoTHI - l2T;
     const float alpha = CR * alpha_B(l);
-    const float beta = P.coll_ion ? beta_coll(l, l2T, rT) : 0.f;
+    // the collisional rate is exactly 0 in FP32 below kTBetaMin, so it is not evaluated there
+    const float beta = (P.coll_ion && Tc > kTBetaMin) ? beta_coll(l, l2T, rT) : 0.f;
     const float Gam = ksig * Nc;
     const float dydt = alpha * n * xi * xi - (Gam + beta * n * xi) * yc;
     float h = rem;
