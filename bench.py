@@ -195,9 +195,13 @@ def ours(args, world, rank, local):
         ty, tz = (int(v) for v in args.tile.split(","))
         a.set_tile(ty, tz)
         tune_ms = None
+        a.set_exec({"tma": A.MODE_FUSED, "ldg": A.MODE_FUSED_LDG}.get(args.kernel, A.MODE_FUSED),
+                   args.graph_batch)
     else:
         ty, tz, tune_ms = a.autotune(3)
-    a.set_exec(A.MODE_FUSED, args.graph_batch)
+    fused_mode = a.get_exec()["mode"]
+    kernel = "k_fused_tma" if fused_mode == A.MODE_FUSED else "k_fused"
+    a.set_exec(fused_mode, args.graph_batch)
     a.step(args.warmup)
     a.synchronize()
     clocks = Clocks(local)
@@ -241,7 +245,7 @@ def ours(args, world, rank, local):
     a.close()
     if args.no_e2e:
         return finish(args, world, rank, dist, st, idx, rate, run, desc, ncell, value, ms, t,
-                      ty, tz, tune_ms, unfused, None, launches, clk, rc, diag, bud)
+                      ty, tz, tune_ms, unfused, None, launches, clk, rc, diag, bud, kernel)
 
     # end to end through the C ABI with host buffers (pinned): state in, every step a source
     # list in and the photon budget out, state out at the end
@@ -254,7 +258,7 @@ def ours(args, world, rank, local):
     b.set_params(bc=A.BC_PERIODIC, sigma_n=run["sigma_n"], sigma_e=run["sigma_e"],
                  e_gamma_eV=run["e_gamma_eV"])
     b.set_tile(ty, tz)
-    b.set_exec(A.MODE_FUSED, args.graph_batch)
+    b.set_exec(fused_mode, args.graph_batch)
     b.set_fields(pin["N"], pin["Fx"], pin["Fy"], pin["Fz"], pin["T"], pin["nH"], y=ypin)
     b.add_sources(idx, rate)
     b.step(1)
@@ -278,11 +282,11 @@ def ours(args, world, rank, local):
                    "+ aton_photon_budget(host) + get_fields(host) once"}
 
     return finish(args, world, rank, dist, st, idx, rate, run, desc, ncell, value, ms, t,
-                  ty, tz, tune_ms, unfused, e2e, launches, clk, rc, diag, bud)
+                  ty, tz, tune_ms, unfused, e2e, launches, clk, rc, diag, bud, kernel)
 
 
 def finish(args, world, rank, dist, st, idx, rate, run, desc, ncell, value, ms, t, ty, tz,
-           tune_ms, unfused, e2e, launches, clk, rc, diag, bud):
+           tune_ms, unfused, e2e, launches, clk, rc, diag, bud, kernel):
     peak, peak_kind = peaks()
     achieved = BYTES_PER_CELL * ncell / (t / args.steps) / 1e9
     kh = kernel_hash()
@@ -292,13 +296,13 @@ def finish(args, world, rank, dist, st, idx, rate, run, desc, ncell, value, ms, 
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "grid": args.grid, "cells": ncell, "sources": len(idx),
-                   "mode": "fused", "graph_batch": args.graph_batch, "tile_ty_tz": [ty, tz],
+                   "mode": kernel, "graph_batch": args.graph_batch, "tile_ty_tz": [ty, tz],
                    "autotune_ms_per_step": tune_ms, "parallelism": f"replicas x{world}",
                    "l2": "no flush: 7.0 GB of state per step >> 126 MB L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind,
                      "traffic": None if traffic is None else traffic * ncell,
-                     "kernel": "k_fused", "bytes_per_cell_update": BYTES_PER_CELL,
+                     "kernel": kernel, "bytes_per_cell_update": BYTES_PER_CELL,
                      "kernel_hash": kh},
         "unfused": unfused,
         "e2e": e2e,
@@ -336,6 +340,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-unfused", action="store_true")
     ap.add_argument("--tile", default="", help="TY,TZ of the fused kernel (skips the autotuner)")
+    ap.add_argument("--kernel", default="tma", choices=["tma", "ldg"],
+                    help="fused kernel used with --tile (the autotuner chooses otherwise)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -47,8 +47,10 @@ extern "C" {
 #define ATON_BC_TRANSMISSIVE 1
 #define ATON_SRC_REPLACE 0
 #define ATON_SRC_APPEND 1
-#define ATON_MODE_FUSED 0      /* one fused transport+source+chemistry kernel per step */
+#define ATON_MODE_FUSED 0      /* one fused transport+source+chemistry kernel per step (TMA-staged
+                                  planes when nx is a multiple of 4, else plain loads) */
 #define ATON_MODE_UNFUSED 1    /* plain three-kernel step (transport; sources; chemistry) */
+#define ATON_MODE_FUSED_LDG 2  /* the fused kernel with plain per-thread loads (no TMA) */
 
 /* photon-budget vector returned by aton_photon_budget [photons] */
 #define ATON_B_EMITTED 0   /* sum of Ndot dt injected by the sources */
@@ -118,17 +120,21 @@ int aton_get_params(aton_handle h, aton_params* p);
  * it alive while the handle uses it. */
 int aton_set_stream(aton_handle h, void* stream);
 
-/* Chooses the kernel path: ATON_MODE_FUSED (default) or ATON_MODE_UNFUSED, and the number of
- * steps captured in one CUDA graph (0: no graphs, plain launches). */
+/* Chooses the kernel path: ATON_MODE_FUSED (default), ATON_MODE_UNFUSED or
+ * ATON_MODE_FUSED_LDG, and the number of steps captured in one CUDA graph (0: no graphs,
+ * plain launches). */
 int aton_set_exec(aton_handle h, int mode, int graph_batch);
+int aton_get_exec(aton_handle h, int* mode, int* graph_batch, int* ty, int* tz);
 
 /* Sets the tile of the fused kernel: ty rows of 32 cells per CTA and tz planes per z-slab.
  * ty in {4, 8, 16}; tz >= 1. */
 int aton_set_tile(aton_handle h, int ty, int tz);
 
-/* Times the fused kernel on a scratch copy of the current state for each candidate tile and
- * keeps the fastest (the simulation state is not advanced). `steps` per candidate (>= 1).
- * Writes the chosen (ty, tz) and its time per step [ms] when the pointers are not NULL. */
+/* Times the fused kernels (TMA-staged where the grid allows it, and plain-load) on a scratch
+ * copy of the current state for each candidate tile and keeps the fastest kernel and tile (the
+ * simulation state is not advanced; an unfused mode stays unfused). `steps` per candidate
+ * (>= 1). Writes the chosen (ty, tz) and its time per step [ms] when the pointers are not NULL;
+ * aton_get_exec reports the chosen mode. */
 int aton_autotune(aton_handle h, int steps, int* ty_out, int* tz_out, float* ms_out);
 
 /* Copies the state in (section 2.2: energy density, flux, temperature, ionisation fraction

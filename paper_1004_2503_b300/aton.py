@@ -17,7 +17,7 @@ ERR_BADARG, ERR_NOMEM, ERR_CUDA, ERR_SUBCYCLE, ERR_NONFINITE, ERR_STATE = -1, -2
 HOST, DEVICE = 0, 1
 BC_PERIODIC, BC_TRANSMISSIVE = 0, 1
 SRC_REPLACE, SRC_APPEND = 0, 1
-MODE_FUSED, MODE_UNFUSED = 0, 1
+MODE_FUSED, MODE_UNFUSED, MODE_FUSED_LDG = 0, 1, 2
 B_EMITTED, B_STORED, B_ABSORBED, B_ESCAPED, B_CLIPPED, B_STORED0 = range(6)
 BUDGET_LEN = 6
 BUDGET_KEYS = ("emitted", "stored", "absorbed", "escaped", "clipped", "stored0")
@@ -25,7 +25,7 @@ BUDGET_KEYS = ("emitted", "stored", "absorbed", "escaped", "clipped", "stored0")
 # every entry point declared in include/aton.h
 EXPORTS = (
     "aton_default_params", "aton_init", "aton_finalize", "aton_set_params", "aton_get_params",
-    "aton_set_stream", "aton_set_exec", "aton_set_tile", "aton_autotune", "aton_set_fields",
+    "aton_set_stream", "aton_set_exec", "aton_get_exec", "aton_set_tile", "aton_autotune", "aton_set_fields",
     "aton_get_fields", "aton_add_sources", "aton_step", "aton_synchronize",
     "aton_photon_budget", "aton_set_budget", "aton_get_diag", "aton_last_error_cells",
     "aton_launches_per_step", "aton_strerror", "aton_last_message", "aton_photon_sum_static",
@@ -80,6 +80,7 @@ def load():
     L.aton_set_stream.argtypes = [_VP, _VP]
     L.aton_set_exec.argtypes = [_VP, C.c_int, C.c_int]
     L.aton_set_tile.argtypes = [_VP, C.c_int, C.c_int]
+    L.aton_get_exec.argtypes = [_VP] + [C.POINTER(C.c_int)] * 4
     L.aton_autotune.argtypes = [_VP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                 C.POINTER(C.c_float)]
     L.aton_set_fields.argtypes = [_VP] + [_VP] * 8 + [C.c_int]
@@ -195,6 +196,11 @@ class Aton:
 
     def set_exec(self, mode=MODE_FUSED, graph_batch=100):
         _check(self.L.aton_set_exec(self.h, int(mode), int(graph_batch)), "aton_set_exec")
+
+    def get_exec(self):
+        v = [C.c_int() for _ in range(4)]
+        _check(self.L.aton_get_exec(self.h, *(C.byref(x) for x in v)), "aton_get_exec")
+        return dict(zip(("mode", "graph_batch", "ty", "tz"), (x.value for x in v)))
 
     def set_tile(self, ty, tz):
         _check(self.L.aton_set_tile(self.h, int(ty), int(tz)), "aton_set_tile")

@@ -86,6 +86,8 @@ struct aton_ctx {
   int graph_batch = 100;
   int ty = 8, tz = 64;
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+  TmaMaps tma[3];          // tile heights 4, 8, 16
+  bool tma_ok[3] = {false, false, false};
 
   cudaStream_t stream() const { return user ? user : own; }
 };
@@ -129,8 +131,11 @@ static int slots_needed(const aton_ctx* h) {
 
 static void free_slots(Slots& s) {
   cudaFree(s.acc); cudaFree(s.sub); cudaFree(s.mx); cudaFree(s.err); cudaFree(s.nan);
+  cudaFree(s.timeout);
   s = Slots{};
 }
+
+static int ty_index(int ty) { return ty == 4 ? 0 : (ty == 8 ? 1 : 2); }
 
 // Adds the slot tallies into the host fold (FP64, fixed order) and clears the slots.
 static int fold_slots(aton_handle h) {
@@ -168,6 +173,7 @@ static int ensure_slots_n(aton_handle h, int need) {
   CU(cudaMalloc(&s.mx, sizeof(unsigned int) * need));
   CU(cudaMalloc(&s.err, sizeof(unsigned int) * need));
   CU(cudaMalloc(&s.nan, sizeof(unsigned int) * need));
+  CU(cudaMalloc(&s.timeout, sizeof(unsigned int)));
   s.n = need;
   h->slots = s;
   cudaStream_t st = h->stream();
@@ -176,6 +182,7 @@ static int ensure_slots_n(aton_handle h, int need) {
   CU(cudaMemsetAsync(s.mx, 0, sizeof(unsigned int) * need, st));
   CU(cudaMemsetAsync(s.err, 0, sizeof(unsigned int) * need, st));
   CU(cudaMemsetAsync(s.nan, 0, sizeof(unsigned int) * need, st));
+  CU(cudaMemsetAsync(s.timeout, 0, sizeof(unsigned int), st));
   return ATON_OK;
 }
 
@@ -262,7 +269,7 @@ static int enqueue_step(aton_handle h, cudaStream_t s) {
   const Fields in{h->f[h->cur][0], h->f[h->cur][1], h->f[h->cur][2], h->f[h->cur][3]};
   const Fields out{h->f[nxt][0], h->f[nxt][1], h->f[nxt][2], h->f[nxt][3]};
   cudaError_t e;
-  if (h->mode == ATON_MODE_FUSED) {
+  if (h->mode == ATON_MODE_FUSED || h->mode == ATON_MODE_FUSED_LDG) {
     FusedArgs a{};
     a.P = step_params(h);
     a.in = in; a.out = out;
@@ -270,7 +277,10 @@ static int enqueue_step(aton_handle h, cudaStream_t s) {
     a.tsrc_start = h->d_tstart; a.tsrc = h->d_tsrc;
     a.slots = h->slots;
     a.tz = h->tz;
-    e = launch_fused(h->ty, a, s);
+    a.in_buf = h->cur;
+    const int ti = ty_index(h->ty);
+    if (h->mode == ATON_MODE_FUSED && h->tma_ok[ti]) e = launch_fused_tma(h->ty, a, h->tma[ti], s);
+    else e = launch_fused(h->ty, a, s);
   } else {
     PlainArgs a{};
     a.P = step_params(h);
@@ -370,6 +380,7 @@ int aton_init(int nx, int ny, int nz, double dx_cm, double c_cms, double dt_s, a
   static bool attrs_done = false;
   if (!attrs_done) {
     e = init_kernel_attributes();
+    if (e == cudaSuccess) e = init_tma_attributes();
     if (e != cudaSuccess) {
       delete h;
       return fail(ATON_ERR_CUDA, "kernel attributes: %s", cudaGetErrorString(e));
@@ -393,6 +404,13 @@ int aton_init(int nx, int ny, int nz, double dx_cm, double c_cms, double dt_s, a
       cudaMalloc(&h->d_bad, sizeof(unsigned int)) != cudaSuccess)
     return bail(fail(ATON_ERR_NOMEM, "cudaMalloc of reduction scratch failed"));
   h->tz = std::min(64, nz);
+  // TMA maps of the fields (row pitch must be a multiple of 16 bytes: nx % 4 == 0)
+  {
+    float* chem[3] = {h->y, h->T, h->nH};
+    const int tys[3] = {4, 8, 16};
+    for (int i = 0; i < 3; ++i)
+      h->tma_ok[i] = make_tma_maps(nx, ny, nz, tys[i], h->f, chem, &h->tma[i]);
+  }
   *out = h;
   return ATON_OK;
 }
@@ -431,8 +449,8 @@ int aton_set_stream(aton_handle h, void* stream) {
 
 int aton_set_exec(aton_handle h, int mode, int graph_batch) {
   if (int rc = check_h(h)) return rc;
-  if (mode != ATON_MODE_FUSED && mode != ATON_MODE_UNFUSED)
-    return fail(ATON_ERR_BADARG, "mode must be ATON_MODE_FUSED or ATON_MODE_UNFUSED");
+  if (mode != ATON_MODE_FUSED && mode != ATON_MODE_UNFUSED && mode != ATON_MODE_FUSED_LDG)
+    return fail(ATON_ERR_BADARG, "mode must be ATON_MODE_FUSED, _UNFUSED or _FUSED_LDG");
   if (graph_batch < 0) return fail(ATON_ERR_BADARG, "graph_batch must be >= 0");
   if (mode != h->mode) {
     if (int rc = fold_slots(h)) return rc;
@@ -440,6 +458,15 @@ int aton_set_exec(aton_handle h, int mode, int graph_batch) {
   h->mode = mode;
   h->graph_batch = graph_batch;
   drop_graphs(h);
+  return ATON_OK;
+}
+
+int aton_get_exec(aton_handle h, int* mode, int* graph_batch, int* ty, int* tz) {
+  if (int rc = check_h(h)) return rc;
+  if (mode) *mode = h->mode;
+  if (graph_batch) *graph_batch = h->graph_batch;
+  if (ty) *ty = h->ty;
+  if (tz) *tz = h->tz;
   return ATON_OK;
 }
 
@@ -592,7 +619,13 @@ static int read_tallies(aton_handle h, double acc[3], unsigned long long u[4], d
   if (stored) CU(launch_sum_field(h->f[h->cur][0], h->ncell, h->d_part, h->d_out + 3, s));
   CU(cudaMemcpyAsync(a, h->d_out, sizeof(a), cudaMemcpyDeviceToHost, s));
   CU(cudaMemcpyAsync(uu, h->d_u64, sizeof(uu), cudaMemcpyDeviceToHost, s));
+  unsigned int tmo = 0;
+  if (h->slots.timeout) CU(cudaMemcpyAsync(&tmo, h->slots.timeout, sizeof(tmo), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
+  if (tmo) {
+    h->latched = ATON_ERR_CUDA;
+    return fail(ATON_ERR_CUDA, "%u CTAs gave up waiting on a pipeline barrier", tmo);
+  }
   if (!h->slots.n) { a[0] = a[1] = a[2] = 0; uu[0] = uu[1] = uu[2] = uu[3] = 0; }
   for (int i = 0; i < 3; ++i) acc[i] = h->fold_acc[i] + a[i];
   u[0] = h->fold_u[0] + uu[0];
@@ -669,7 +702,7 @@ int aton_last_error_cells(aton_handle h, int64_t* count) {
 int aton_launches_per_step(aton_handle h, int* launches) {
   if (int rc = check_h(h)) return rc;
   if (!launches) return fail(ATON_ERR_BADARG, "launches is NULL");
-  if (h->mode == ATON_MODE_FUSED) *launches = 1;
+  if (h->mode == ATON_MODE_FUSED || h->mode == ATON_MODE_FUSED_LDG) *launches = 1;
   else *launches = h->src_n > 0 ? plain_launches() : plain_launches() - 1;
   return ATON_OK;
 }
@@ -696,7 +729,6 @@ int aton_autotune(aton_handle h, int steps, int* ty_out, int* tz_out, float* ms_
     CU(cudaMemcpyAsync(save[q], src[q], fb, cudaMemcpyDeviceToDevice, s));
   }
   const int mode0 = h->mode, gb0 = h->graph_batch, ty0 = h->ty, tz0 = h->tz, cur0 = h->cur;
-  h->mode = ATON_MODE_FUSED;
   h->graph_batch = 0;
   int best_ty = ty0, best_tz = tz0;
   float best = 1e30f;
@@ -705,11 +737,16 @@ int aton_autotune(aton_handle h, int steps, int* ty_out, int* tz_out, float* ms_
   CU(cudaEventCreate(&e1));
   const int tys[3] = {4, 8, 16};
   const int tzs[5] = {16, 32, 64, 128, 256};
+  int best_mode = ATON_MODE_FUSED;
   int rc = ATON_OK;
+  for (int kind = 0; kind < 2 && rc == ATON_OK; ++kind)
   for (int a = 0; a < 3 && rc == ATON_OK; ++a)
     for (int b = 0; b < 5 && rc == ATON_OK; ++b) {
       const int tz = std::min(tzs[b], h->nz);
       if (b > 0 && tz == std::min(tzs[b - 1], h->nz)) continue;
+      // kind 0: the TMA-staged kernel (when the grid allows it), kind 1: plain loads
+      if (kind == 0 && !h->tma_ok[ty_index(tys[a])]) continue;
+      h->mode = kind == 0 ? ATON_MODE_FUSED : ATON_MODE_FUSED_LDG;
       h->ty = tys[a];
       h->tz = tz;
       h->tiles_dirty = true;
@@ -727,7 +764,7 @@ int aton_autotune(aton_handle h, int steps, int* ty_out, int* tz_out, float* ms_
       float ms = 0;
       cudaEventElapsedTime(&ms, e0, e1);
       ms /= steps;
-      if (ms < best) { best = ms; best_ty = h->ty; best_tz = h->tz; }
+      if (ms < best) { best = ms; best_ty = h->ty; best_tz = h->tz; best_mode = h->mode; }
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -747,7 +784,8 @@ int aton_autotune(aton_handle h, int steps, int* ty_out, int* tz_out, float* ms_
     CU(cudaMemsetAsync(h->slots.err, 0, sizeof(unsigned int) * h->slots.n, st));
     CU(cudaMemsetAsync(h->slots.nan, 0, sizeof(unsigned int) * h->slots.n, st));
   }
-  h->mode = mode0;
+  // keep the caller's choice of the unfused path; otherwise take the faster fused kernel
+  h->mode = mode0 == ATON_MODE_UNFUSED ? mode0 : best_mode;
   h->graph_batch = gb0;
   h->ty = best_ty;
   h->tz = best_tz;

@@ -1,6 +1,7 @@
 // aton_internal.h -- shared declarations of the libaton.so host code and kernels (not part
 // of the public C ABI, which is include/aton.h).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,7 +33,14 @@ struct Slots {
   unsigned int* mx = nullptr;         // [n]: max sub-steps of a cell
   unsigned int* err = nullptr;        // [n]: cells at the sub-cycle cap
   unsigned int* nan = nullptr;        // [n]: non-finite cells
+  unsigned int* timeout = nullptr;    // [1]: pipeline waits that gave up (must stay 0)
   int n = 0;
+};
+
+// Tensor maps of the TMA-staged fused kernel (one set per tile height).
+struct TmaMaps {
+  CUtensorMap u[2][4];   // ping-pong buffer x (N, Fx, Fy, Fz), box (32+8) x (ty+2) x 1
+  CUtensorMap chem[3];   // y, T, nH, box 32 x ty x 1
 };
 
 struct Fields {
@@ -52,6 +60,7 @@ struct FusedArgs {
   const TileSrc* tsrc;
   Slots slots;
   int tz;
+  int in_buf;   // ping-pong index of `in` (selects the TMA maps)
 };
 
 struct PlainArgs {
@@ -71,6 +80,10 @@ void set_last_message(const char* msg);
 
 // ---- launchers (aton_kernels.cu) ----
 cudaError_t init_kernel_attributes();
+cudaError_t init_tma_attributes();
+cudaError_t launch_fused_tma(int ty, const FusedArgs& a, const TmaMaps& m, cudaStream_t s);
+bool make_tma_maps(int nx, int ny, int nz, int ty, float* const u[2][4], float* const chem[3],
+                   TmaMaps* out);
 cudaError_t launch_fused(int ty, const FusedArgs& a, cudaStream_t s);
 int fused_tiles(int nx, int ny, int nz, int ty, int tz);
 cudaError_t launch_plain_step(const PlainArgs& a, cudaStream_t s);

@@ -1,0 +1,382 @@
+// aton_tma.cu -- the fused step kernel with TMA-staged planes (sm_103a).
+//
+// Same step as k_fused (Lax-Friedrichs M1 transport, section 2.2 and Appendix Eqs. A2/A5;
+// sources, section 2.3; chemistry operator Phi, Appendix Eq. A4), with the plane loads moved
+// off the compute threads. One producer warp streams each z-plane of the CTA's 32 x TY column
+// tile into a four-deep shared-memory ring with cp.async.bulk.tensor: a (32+8) x (TY+2) box of
+// each of N, Fx, Fy, Fz (one-cell halo; the x origin is 4 cells left so it stays 16-byte
+// aligned) and a 32 x TY box of y, T, nH. mbarriers signal full and empty stages. The TY
+// consumer warps turn each landed plane into a three-plane ring of vector records per slot,
+// (N, F/c), (Dxx, Dxy, Dxz, Dyy) N and (Dyz, Dzz) N, patching the slots that lie outside the
+// grid from global memory (boundary map; edge tiles only) and computing N D once per slot;
+// a neighbour then costs two or three vector loads. The cell update is the same as in
+// k_fused. Several planes are in flight per CTA without holding them in registers.
+//
+// Used when nx is a multiple of 4 (the tensor-map row pitch must be a multiple of 16 bytes);
+// otherwise the step falls back to k_fused.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include "aton_internal.h"
+#include "aton_step_common.cuh"
+
+namespace aton {
+
+namespace {
+
+constexpr int kStages = 4;
+constexpr int kBoxX = kTileX + 8;          // x0-4 .. x0+35
+constexpr unsigned kWaitLimit = 1u << 26;  // polls before a wait is declared failed
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait on the phase with the given parity. Returns false (and the caller raises the
+// error word) if the phase did not complete within kWaitLimit polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  const unsigned a = smem_u32(bar);
+  for (unsigned i = 0; i < kWaitLimit; ++i) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void consumer_bar(int nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+template <int TY>
+struct Layout {
+  static constexpr int PL = kBoxX * (TY + 2);             // floats per field-plane (with halo)
+  static constexpr int PLP = (PL + 31) & ~31;             // padded to 128 bytes
+  static constexpr int CH = kTileX * TY;                  // chemistry box floats
+  static constexpr int STAGE = 4 * PLP + 3 * CH;          // floats per stage
+  static constexpr int RX = kTileX + 2;                   // ring row pitch (one-cell halo)
+  static constexpr int PLR = RX * (TY + 2);               // ring slots per plane
+  static constexpr unsigned U_BYTES = 4u * PL * 4u;       // bytes landed per plane (u)
+  static constexpr unsigned C_BYTES = 3u * CH * 4u;       // bytes landed per plane (chem)
+  static constexpr size_t STAGE_BYTES = (size_t)kStages * STAGE * 4;
+  static constexpr size_t RING_BYTES = (size_t)3 * PLR * (16 + 16 + 8);
+  static constexpr size_t BYTES = STAGE_BYTES + RING_BYTES + 2 * kStages * 8 + 128;
+};
+
+}  // namespace
+
+template <int TY, bool PER>
+__global__ void __launch_bounds__(kTileX * (TY + 1)) k_fused_tma(const FusedArgs A,
+                                                                 const __grid_constant__ TmaMaps M) {
+  using L = Layout<TY>;
+  constexpr int TX = kTileX, NH = 2 * TX + 2 * TY, NC = TX * TY;
+  extern __shared__ __align__(128) float sm_raw[];
+  float* sm = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(sm_raw) + 127) & ~uintptr_t(127));
+  float* stage0 = sm;
+  // ring of prepared planes: (N, Fx/c, Fy/c, Fz/c), (Dxx, Dxy, Dxz, Dyy) N, (Dyz, Dzz) N
+  float4* RU = reinterpret_cast<float4*>(sm + kStages * L::STAGE);
+  float4* RA = RU + 3 * L::PLR;
+  float2* RB = reinterpret_cast<float2*>(RA + 3 * L::PLR);
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(RB + 3 * L::PLR);
+  unsigned long long* empty = full + kStages;
+
+  const StepParams& P = A.P;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
+  const int nx = P.nx, ny = P.ny, nz = P.nz;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * A.tz;
+  const int z1 = min(z0 + A.tz, nz);
+  const int nplanes = z1 - z0 + 2;   // planes z0-1 .. z1
+  const long long plane = (long long)nx * ny;
+  const int tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  bool failed = false;
+
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], TY);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  Tally tl;
+  if (ty == TY) {
+    // ---------------- producer warp: one lane issues the plane loads ----------------
+    if (tx == 0) {
+      for (int k = 0; k < nplanes; ++k) {
+        const int s = k % kStages;
+        if (k >= kStages && !mbar_wait(&empty[s], ((k / kStages) - 1) & 1)) failed = true;
+        int p = z0 - 1 + k;   // in [-1, nz]
+        if (p < 0) p = PER ? nz - 1 : 0;
+        if (p >= nz) p = PER ? 0 : nz - 1;
+        const bool chem = k >= 1 && k <= z1 - z0;
+        mbar_expect_tx(&full[s], L::U_BYTES + (chem ? L::C_BYTES : 0u));
+        float* st = stage0 + s * L::STAGE;
+        for (int q = 0; q < 4; ++q)
+          tma_load_3d(st + q * L::PLP, &M.u[A.in_buf][q], x0 - 4, y0 - 1, p, &full[s]);
+        if (chem)
+          for (int q = 0; q < 3; ++q)
+            tma_load_3d(st + 4 * L::PLP + q * L::CH, &M.chem[q], x0, y0, p, &full[s]);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---------------- consumer warps ----------------
+    const int gx = x0 + tx, gy = y0 + ty;
+    const bool act = gx < nx && gy < ny;
+    const int oslot = (ty + 1) * kBoxX + (tx + 4);       // stage slot
+    const int orslot = (ty + 1) * L::RX + (tx + 1);      // ring slot
+    // halo slot of this thread (if any) in tile coordinates
+    int hx = 0, hy = 0, hslot = -1, hrslot = -1;
+    if (tid < NH) {
+      if (tid < TX) { hx = tid; hy = -1; }
+      else if (tid < 2 * TX) { hx = tid - TX; hy = TY; }
+      else if (tid < 2 * TX + TY) { hx = -1; hy = tid - 2 * TX; }
+      else { hx = TX; hy = tid - 2 * TX - TY; }
+      hslot = (hy + 1) * kBoxX + (hx + 4);
+      hrslot = (hy + 1) * L::RX + (hx + 1);
+    }
+    const bool own_out = !act;
+    const bool halo_out = hslot >= 0 && (x0 + hx < 0 || x0 + hx >= nx || y0 + hy < 0 || y0 + hy >= ny);
+    const long long ocol = bc_map(gx, nx, PER) + (long long)nx * bc_map(gy, ny, PER);
+    const long long hcol = hslot >= 0 ? bc_map(x0 + hx, nx, PER) + (long long)nx * bc_map(y0 + hy, ny, PER) : 0;
+    const float rc = P.rc, cl = P.c, lam = P.lam;
+    const float hl = 0.5f * lam, cu = 1.f - 3.f * lam;
+    const float* __restrict__ gN = A.in.N;
+    const float* __restrict__ gX = A.in.Fx;
+    const float* __restrict__ gY = A.in.Fy;
+    const float* __restrict__ gZ = A.in.Fz;
+
+    // (N, F/c) of a slot of stage `st`: patched from global memory (boundary map) when the slot
+    // lies outside the grid, read from the TMA box otherwise.
+    auto prep = [&](const float* st, int slot, bool out, long long col, int p) {
+      float4 u;
+      if (out) {
+        const long long o = (long long)p * plane + col;
+        u = make_float4(__ldg(gN + o), __ldg(gX + o) * rc, __ldg(gY + o) * rc, __ldg(gZ + o) * rc);
+      } else {
+        u = make_float4(st[slot], st[L::PLP + slot] * rc, st[2 * L::PLP + slot] * rc,
+                        st[3 * L::PLP + slot] * rc);
+      }
+      return u;
+    };
+    // the prepared slot into ring plane r; returns the z flux (Fz/c, Dxz, Dyz, Dzz) N
+    auto put = [&](int r, int rslot, const float4& u) {
+      const ND6 d = m1_pressure(u.x, u.y, u.z, u.w);
+      RU[r * L::PLR + rslot] = u;
+      RA[r * L::PLR + rslot] = make_float4(d.xx, d.xy, d.xz, d.yy);
+      RB[r * L::PLR + rslot] = make_float2(d.yz, d.zz);
+      return make_float4(u.w, d.xz, d.yz, d.zz);
+    };
+    auto release = [&](int k) {
+      __syncwarp();
+      if (tx == 0) mbar_arrive(&empty[k % kStages]);
+    };
+    auto plane_of = [&](int z) {   // z in [-1, nz]
+      return z < 0 ? (PER ? nz - 1 : 0) : (z >= nz ? (PER ? 0 : nz - 1) : z);
+    };
+
+    float4 um, pm, uc, pc;
+    // plane z0-1: the own column's state and z flux only
+    {
+      if (!mbar_wait(&full[0], 0)) failed = true;
+      um = prep(stage0, oslot, own_out, ocol, plane_of(z0 - 1));
+      const ND6 d = m1_pressure(um.x, um.y, um.z, um.w);
+      pm = make_float4(um.w, d.xz, d.yz, d.zz);
+      release(0);
+    }
+    // plane z0 into ring plane 1
+    {
+      if (!mbar_wait(&full[1 % kStages], 0)) failed = true;
+      const float* st = stage0 + (1 % kStages) * L::STAGE;
+      const int p = plane_of(z0);
+      uc = prep(st, oslot, own_out, ocol, p);
+      pc = put(1, orslot, uc);
+      if (hslot >= 0) put(1, hrslot, prep(st, hslot, halo_out, hcol, p));
+    }
+    int sp = A.tsrc_start[tile];
+    const int se = A.tsrc_start[tile + 1];
+    long long o = (long long)z0 * plane + ocol;
+
+    for (int z = z0; z < z1; ++z, o += plane) {
+      const int k = z - z0 + 1;           // plane index of z
+      const int kn = k + 1;               // plane z+1
+      float4 up, pp;
+      {
+        if (!mbar_wait(&full[kn % kStages], (kn / kStages) & 1)) failed = true;
+        const float* st = stage0 + (kn % kStages) * L::STAGE;
+        const int p = plane_of(z + 1);
+        const int r = kn % 3;
+        up = prep(st, oslot, own_out, ocol, p);
+        pp = put(r, orslot, up);
+        if (hslot >= 0) put(r, hrslot, prep(st, hslot, halo_out, hcol, p));
+      }
+      consumer_bar(TX * TY);
+      if (act) {
+        const int r = k % 3;
+        const float4* U = RU + r * L::PLR + orslot;
+        const float4* Q = RA + r * L::PLR + orslot;
+        const float2* B = RB + r * L::PLR + orslot;
+        constexpr int RX = L::RX;
+        const float4 uL = U[-1], uR = U[1], uD = U[-RX], uU = U[RX];
+        const float4 aL = Q[-1], aR = Q[1], aD = Q[-RX], aU = Q[RX];
+        const float2 bD = B[-RX], bU = B[RX];
+        // sum over the six faces of (flux difference) - (neighbour sum); new u = (1-3 lam) u
+        // - lam/2 * that, the Lax-Friedrichs update written around the centre value.
+        // x faces carry (Fx, Dxx, Dxy, Dxz), y faces (Fy, Dxy, Dyy, Dyz), z (Fz, Dxz, Dyz, Dzz).
+        const float sN = (uR.y - uL.y) + (uU.z - uD.z) + (pp.x - pm.x) -
+                         ((uR.x + uL.x) + (uU.x + uD.x) + (up.x + um.x));
+        const float sX = (aR.x - aL.x) + (aU.y - aD.y) + (pp.y - pm.y) -
+                         ((uR.y + uL.y) + (uU.y + uD.y) + (up.y + um.y));
+        const float sY = (aR.y - aL.y) + (aU.w - aD.w) + (pp.z - pm.z) -
+                         ((uR.z + uL.z) + (uU.z + uD.z) + (up.z + um.z));
+        const float sZ = (aR.z - aL.z) + (bU.x - bD.x) + (pp.w - pm.w) -
+                         ((uR.w + uL.w) + (uU.w + uD.w) + (up.w + um.w));
+        float Nn = cu * uc.x - hl * sN;
+        float Xn = cu * uc.y - hl * sX;
+        float Yn = cu * uc.z - hl * sY;
+        float Zn = cu * uc.w - hl * sZ;
+        if (!PER) {
+          float e = 0.f;
+          if (gx == 0) e -= uc.y;
+          if (gx == nx - 1) e += uc.y;
+          if (gy == 0) e -= uc.z;
+          if (gy == ny - 1) e += uc.z;
+          if (z == 0) e -= uc.w;
+          if (z == nz - 1) e += uc.w;
+          if (e != 0.f) tl.escaped.add(lam * e);
+        }
+        clamp_state(Nn, Xn, Yn, Zn, tl.clipped);
+        while (sp < se) {
+          const TileSrc s = A.tsrc[sp];
+          if (s.z != z) break;
+          if (s.cell == tid) Nn += s.dN;
+          ++sp;
+        }
+        const float* C = stage0 + (k % kStages) * L::STAGE + 4 * L::PLP + tid;
+        float cy = C[0], cT = C[L::CH];
+        const float cn = C[2 * L::CH];
+        const float N0 = Nn;
+        const ChemOut co = chem_cell(P, cn, Nn, Xn, Yn, Zn, cy, cT);
+        tl.absorbed.add(N0 - Nn);
+        tl.sub += co.nsub;
+        tl.mx = max(tl.mx, (unsigned)co.nsub);
+        tl.err += co.err;
+        if (!isfinite(Nn) || !isfinite(cT) || !isfinite(Xn + Yn + Zn)) tl.nan += 1;
+        A.out.N[o] = Nn; A.out.Fx[o] = Xn * cl; A.out.Fy[o] = Yn * cl; A.out.Fz[o] = Zn * cl;
+        A.y[o] = cy; A.T[o] = cT;
+      }
+      release(k);
+      um = uc; pm = pc; uc = up; pc = pp;
+    }
+    (void)NC;
+  }
+  if (failed) atomicAdd(A.slots.timeout, 1u);
+  flush_tally<TY + 1>(tl, A.slots, tile);
+}
+
+namespace {
+
+template <int TY, bool PER>
+cudaError_t set_tma_attr() {
+  return cudaFuncSetAttribute(k_fused_tma<TY, PER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Layout<TY>::BYTES);
+}
+
+template <int TY, bool PER>
+cudaError_t launch_tma_t(const FusedArgs& a, const TmaMaps& m, cudaStream_t s) {
+  dim3 grid((a.P.nx + kTileX - 1) / kTileX, (a.P.ny + TY - 1) / TY, (a.P.nz + a.tz - 1) / a.tz);
+  dim3 block(kTileX, TY + 1);
+  k_fused_tma<TY, PER><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t init_tma_attributes() {
+  cudaError_t e;
+  if ((e = set_tma_attr<4, true>()) != cudaSuccess) return e;
+  if ((e = set_tma_attr<4, false>()) != cudaSuccess) return e;
+  if ((e = set_tma_attr<8, true>()) != cudaSuccess) return e;
+  if ((e = set_tma_attr<8, false>()) != cudaSuccess) return e;
+  if ((e = set_tma_attr<16, true>()) != cudaSuccess) return e;
+  return set_tma_attr<16, false>();
+}
+
+cudaError_t launch_fused_tma(int ty, const FusedArgs& a, const TmaMaps& m, cudaStream_t s) {
+  const bool per = a.P.bc == 0;
+  switch (ty) {
+    case 4: return per ? launch_tma_t<4, true>(a, m, s) : launch_tma_t<4, false>(a, m, s);
+    case 8: return per ? launch_tma_t<8, true>(a, m, s) : launch_tma_t<8, false>(a, m, s);
+    case 16: return per ? launch_tma_t<16, true>(a, m, s) : launch_tma_t<16, false>(a, m, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Tensor maps of the grid fields for a tile height ty: for each ping-pong buffer and each of
+// N, Fx, Fy, Fz a (32+8) x (ty+2) x 1 box, and 32 x ty x 1 boxes of y, T, nH. Returns false if
+// the driver entry point is unavailable or an encode fails (the caller then uses k_fused).
+bool make_tma_maps(int nx, int ny, int nz, int ty, float* const u[2][4], float* const chem[3],
+                   TmaMaps* out) {
+  if (nx % 4 != 0) return false;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const cuuint32_t box_u[3] = {(cuuint32_t)kBoxX, (cuuint32_t)(ty + 2), 1};
+  const cuuint32_t box_c[3] = {(cuuint32_t)kTileX, (cuuint32_t)ty, 1};
+  for (int b = 0; b < 2; ++b)
+    for (int q = 0; q < 4; ++q)
+      if (encode(&out->u[b][q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, u[b][q], dims, strides, box_u,
+                 estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+          CUDA_SUCCESS)
+        return false;
+  for (int q = 0; q < 3; ++q)
+    if (encode(&out->chem[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, chem[q], dims, strides, box_c,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+      return false;
+  return true;
+}
+
+}  // namespace aton

@@ -58,7 +58,9 @@ def test_stromgren_32_transmissive(fixed_T):
 
 
 @pytest.mark.parametrize("shape,tile", [((40, 1, 1), (4, 7)), ((2, 3, 5), (8, 1)),
-                                        ((9, 17, 33), (4, 4)), ((3, 40, 70), (16, 2))])
+                                        ((9, 17, 33), (4, 4)), ((3, 40, 70), (16, 2)),
+                                        ((9, 17, 36), (4, 4)), ((3, 40, 68), (16, 2)),
+                                        ((7, 5, 4), (8, 3))])
 def test_ragged_and_degenerate_shapes(shape, tile):
     st, idx, rate, run = W.workload_small(shape=shape, nsrc=2, seed_field=11, seed_src=12)
     orc, _, _ = run_oracle(st, idx, rate, run, 30)
@@ -67,6 +69,25 @@ def test_ragged_and_degenerate_shapes(shape, tile):
         assert rc == 0
         assert_gates(errors(f, orc), (shape, tile, mode))
         assert abs(budget_closure(b)) <= 1e-6
+
+
+@pytest.mark.parametrize("shape,tile", [((20, 24, 36), (8, 64)), ((9, 13, 44), (4, 3)),
+                                        ((5, 7, 8), (16, 2)), ((12, 40, 96), (8, 5))])
+def test_tma_staged_and_plain_load_fused_kernels_agree(shape, tile):
+    """The TMA-staged fused kernel (nx a multiple of 4) and the plain-load fused kernel do the
+    same arithmetic; separately compiled, they agree to 1e-5 (contraction may differ)."""
+    st, idx, rate, run = W.workload_small(shape=shape, nsrc=3, seed_field=31, seed_src=32)
+    for bc in ("periodic", "transmissive"):
+        r = dict(run, bc=bc)
+        f1, b1, d1, rc1 = run_gpu(st, idx, rate, r, 20, mode=A.MODE_FUSED, tile=tile)
+        f2, b2, d2, rc2 = run_gpu(st, idx, rate, r, 20, mode=A.MODE_FUSED_LDG, tile=tile)
+        assert rc1 == 0 and rc2 == 0
+        for k in ("N", "Fx", "Fy", "Fz", "y", "T"):
+            scale = np.abs(f2[k]).max()
+            assert np.abs(f1[k] - f2[k]).max() <= 1e-5 * scale, (bc, k)
+        assert b1["absorbed"] == pytest.approx(b2["absorbed"], rel=1e-5)
+        assert b1["escaped"] == pytest.approx(b2["escaped"], rel=1e-5, abs=1e-9 * b2["emitted"])
+        assert d1["substeps_total"] == pytest.approx(d2["substeps_total"], rel=1e-4)
 
 
 def test_fused_equals_unfused_closely(small):
@@ -263,3 +284,21 @@ def test_chemistry_of_single_cells_matches_the_oracle():
             worst["N"] = max(worst["N"], abs(g["N"] - r["N"]) / r["N"])
     print("single-cell worst", worst)
     assert worst["x"] <= 1e-3 and worst["T"] <= 1e-3 and worst["N"] <= 1e-3, worst
+
+
+def test_autotune_leaves_the_state_untouched(small):
+    st, idx, rate, run = small
+    a = A.from_workload(st, idx, rate, run)
+    a.step(3)
+    before = a.get_fields()
+    b0 = a.photon_budget()
+    ty, tz, ms = a.autotune(1)
+    assert ty in (4, 8, 16) and 1 <= tz <= run["nz"] and ms > 0
+    assert a.get_exec()["mode"] in (A.MODE_FUSED, A.MODE_FUSED_LDG)
+    after = a.get_fields()
+    for k in before:
+        assert np.array_equal(before[k], after[k]), k
+    assert a.photon_budget() == b0
+    a.step(2)
+    assert a.synchronize() == 0
+    a.close()
