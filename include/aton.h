@@ -63,6 +63,7 @@ extern "C" {
 /* identity: stored0 + emitted = stored + absorbed + escaped + clipped */
 
 typedef struct aton_ctx* aton_handle;
+typedef struct aton_mlp* aton_mlp_handle;
 
 /* Physical and numerical parameters. Defaults (aton_default_params) are the paper's single
  * group for a 50 000 K black body (section 2.2: sigma_e 2.49e-18, sigma_n 2.93e-18 cm^2,
@@ -93,7 +94,15 @@ typedef struct {
   int64_t substeps_max;     /* largest sub-step count of any cell in any step */
   int64_t error_cells;      /* cell-steps that reached the sub-cycle cap */
   int64_t nonfinite_cells;  /* cell-steps that produced a non-finite value */
+  int64_t surrogate_cells;  /* cell-steps whose chemistry the surrogate replaced */
 } aton_diag;
+
+/* Chemistry surrogate in the step (see aton_set_surrogate). */
+typedef struct {
+  int enabled;           /* nonzero: offer cells to the network */
+  double gate_substeps;  /* offer a cell when its explicit sub-step estimate is >= this */
+  double residual_max;   /* accept a prediction when its photon residual is <= this */
+} aton_surrogate_params;
 
 /* Fills *p with the defaults above. Never fails. */
 void aton_default_params(aton_params* p);
@@ -208,6 +217,56 @@ int aton_launches_per_step(aton_handle h, int* launches);
  * device memory of the current device), CUDA. */
 int aton_photon_sum_static(const float* N, int64_t n, double cell_volume, double* out,
                            void* stream);
+
+/* ---- chemistry surrogate (spec learned part; not in the paper) ----
+ * A 5 -> 64 -> 64 -> 3 SiLU network on BF16 tensor cores (FP32 accumulation) that replaces the
+ * sub-cycled chemistry operator Phi (Appendix Eq. A4) for cells that would sub-cycle heavily.
+ * Features: (log10 nH, log10 y, log10 T, log10 N, log10 dt); targets: the changes of log10 y,
+ * log10 T and log10 N over dt; both standardised by aton_mlp_fit_norm. Parameters are one
+ * float vector (W1 64x5, b1, W2 64x64, b2, W3 3x64, b3; aton_mlp_num_params() floats). Pair
+ * records are 8 floats: nH, N, y, T (operator input), N', y', T' (output), sub-steps taken.
+ * All array arguments are device pointers unless `where` says otherwise; calls synchronise. */
+
+/* Records, for every `stride`-th cell (offset rotating with the step), the chemistry operator's
+ * input and output at each following step into `records` (device, capacity records of 8
+ * floats; NULL stops). Step s writes slots [s P, (s+1) P), P = ceil(ncell / stride), record
+ * j of cell j * stride + (s mod stride); slots whose cell falls beyond the grid are left as
+ * they were. While set, steps run the plain three-kernel path without graphs. */
+int aton_set_pair_sink(aton_handle h, float* records, int64_t capacity, int stride);
+int aton_pair_count(aton_handle h, int64_t* count);
+
+/* Uses network m in the chemistry of later steps (NULL or enabled = 0: off). The handle keeps
+ * the pointer; m must outlive its use. Steps then run the plain path with the surrogate
+ * chemistry kernel. A cell is offered to the network when its explicit sub-step estimate from
+ * photo-ionisation and photo-heating is >= gate_substeps and its features lie in the training
+ * range; a prediction is accepted when
+ * its photons absorbed per atom match the atoms ionised plus the recombinations over dt within
+ * residual_max of max(y, 1e-8); every other cell takes the exact operator. */
+void aton_default_surrogate_params(aton_surrogate_params* p);
+int aton_set_surrogate(aton_handle h, aton_mlp_handle m, const aton_surrogate_params* p);
+
+int aton_mlp_create(aton_mlp_handle* out, unsigned long long seed);
+void aton_mlp_destroy(aton_mlp_handle m);
+int aton_mlp_num_params(void);
+int aton_mlp_set_params(aton_mlp_handle m, const float* theta, int where);
+int aton_mlp_get_params(aton_mlp_handle m, float* theta, int where);
+/* standardisation from pair records; the normalisation block is 26 floats: input mean[5],
+ * scale[5], output mean[3], scale[3], input min[5], max[5] */
+int aton_mlp_fit_norm(aton_mlp_handle m, const float* records, int64_t n, double dt);
+int aton_mlp_get_norm(aton_mlp_handle m, float* out);
+int aton_mlp_set_norm(aton_mlp_handle m, const float* in);
+/* standardised features X (n x 5) and targets T (n x 3, may be NULL) of pair records */
+int aton_mlp_features(aton_mlp_handle m, const float* records, int64_t n, double dt, float* X,
+                      float* T);
+/* network outputs Y (n x 3) of standardised features X */
+int aton_mlp_forward(aton_mlp_handle m, const float* X, int64_t n, float* Y);
+/* mean squared error and its gradient (device, num_params floats) over a batch */
+int aton_mlp_loss_grad(aton_mlp_handle m, const float* X, const float* T, int n, float* grad,
+                       double* loss);
+/* one Adam step (beta 0.9, 0.999, eps 1e-8) on a batch; loss may be NULL (no wait) */
+int aton_mlp_train_step(aton_mlp_handle m, const float* X, const float* T, int n, float lr,
+                        double* loss);
+int aton_mlp_synchronize(aton_mlp_handle m);
 
 /* Static description of a status code. */
 const char* aton_strerror(int code);

@@ -29,6 +29,11 @@ EXPORTS = (
     "aton_get_fields", "aton_add_sources", "aton_step", "aton_synchronize",
     "aton_photon_budget", "aton_set_budget", "aton_get_diag", "aton_last_error_cells",
     "aton_launches_per_step", "aton_strerror", "aton_last_message", "aton_photon_sum_static",
+    "aton_set_pair_sink", "aton_pair_count", "aton_default_surrogate_params", "aton_set_surrogate",
+    "aton_mlp_create", "aton_mlp_destroy", "aton_mlp_num_params", "aton_mlp_set_params",
+    "aton_mlp_get_params", "aton_mlp_fit_norm", "aton_mlp_get_norm", "aton_mlp_set_norm",
+    "aton_mlp_features", "aton_mlp_forward", "aton_mlp_loss_grad", "aton_mlp_train_step",
+    "aton_mlp_synchronize",
 )
 
 
@@ -46,7 +51,11 @@ class aton_params(C.Structure):
 class aton_diag(C.Structure):
     _fields_ = [("steps", C.c_int64), ("substeps_total", C.c_int64),
                 ("substeps_max", C.c_int64), ("error_cells", C.c_int64),
-                ("nonfinite_cells", C.c_int64)]
+                ("nonfinite_cells", C.c_int64), ("surrogate_cells", C.c_int64)]
+
+
+class aton_surrogate_params(C.Structure):
+    _fields_ = [("enabled", C.c_int), ("gate_substeps", C.c_double), ("residual_max", C.c_double)]
 
 
 class AtonError(RuntimeError):
@@ -96,6 +105,25 @@ def load():
     L.aton_strerror.argtypes = [C.c_int]
     L.aton_strerror.restype = C.c_char_p
     L.aton_photon_sum_static.argtypes = [_VP, C.c_int64, C.c_double, C.POINTER(C.c_double), _VP]
+    L.aton_set_pair_sink.argtypes = [_VP, _VP, C.c_int64, C.c_int]
+    L.aton_pair_count.argtypes = [_VP, C.POINTER(C.c_int64)]
+    L.aton_default_surrogate_params.argtypes = [C.POINTER(aton_surrogate_params)]
+    L.aton_default_surrogate_params.restype = None
+    L.aton_set_surrogate.argtypes = [_VP, _VP, C.POINTER(aton_surrogate_params)]
+    L.aton_mlp_create.argtypes = [C.POINTER(_VP), C.c_ulonglong]
+    L.aton_mlp_destroy.argtypes = [_VP]
+    L.aton_mlp_destroy.restype = None
+    L.aton_mlp_num_params.argtypes = []
+    L.aton_mlp_set_params.argtypes = [_VP, _VP, C.c_int]
+    L.aton_mlp_get_params.argtypes = [_VP, _VP, C.c_int]
+    L.aton_mlp_fit_norm.argtypes = [_VP, _VP, C.c_int64, C.c_double]
+    L.aton_mlp_get_norm.argtypes = [_VP, _VP]
+    L.aton_mlp_set_norm.argtypes = [_VP, _VP]
+    L.aton_mlp_features.argtypes = [_VP, _VP, C.c_int64, C.c_double, _VP, _VP]
+    L.aton_mlp_forward.argtypes = [_VP, _VP, C.c_int64, _VP]
+    L.aton_mlp_loss_grad.argtypes = [_VP, _VP, _VP, C.c_int, _VP, C.POINTER(C.c_double)]
+    L.aton_mlp_train_step.argtypes = [_VP, _VP, _VP, C.c_int, C.c_float, C.POINTER(C.c_double)]
+    L.aton_mlp_synchronize.argtypes = [_VP]
     L.aton_last_message.argtypes = []
     L.aton_last_message.restype = C.c_char_p
     for name in EXPORTS:
@@ -269,6 +297,25 @@ class Aton:
         _check(self.L.aton_last_error_cells(self.h, C.byref(n)), "aton_last_error_cells")
         return n.value
 
+    def set_pair_sink(self, records, stride=1):
+        """records: a float32 torch CUDA tensor of shape (capacity, 8), or None to stop."""
+        if records is None:
+            _check(self.L.aton_set_pair_sink(self.h, None, 0, 1), "aton_set_pair_sink")
+            return
+        _check(self.L.aton_set_pair_sink(self.h, records.data_ptr(), int(records.shape[0]),
+                                         int(stride)), "aton_set_pair_sink")
+
+    def pair_count(self):
+        n = C.c_int64()
+        _check(self.L.aton_pair_count(self.h, C.byref(n)), "aton_pair_count")
+        return n.value
+
+    def set_surrogate(self, mlp, gate_substeps=8.0, residual_max=1e-4, enabled=True):
+        p = aton_surrogate_params(int(bool(enabled)), float(gate_substeps), float(residual_max))
+        _check(self.L.aton_set_surrogate(self.h, None if mlp is None else mlp.h,
+                                         None if mlp is None else C.byref(p)), "aton_set_surrogate")
+        self._sur = mlp   # keep the network alive while the handle may use it
+
     def launches_per_step(self):
         n = C.c_int()
         _check(self.L.aton_launches_per_step(self.h, C.byref(n)), "aton_launches_per_step")
@@ -285,6 +332,85 @@ def photon_sum_static(N, cell_volume, stream=None):
     _check(load().aton_photon_sum_static(ptr, int(N.numel()), float(cell_volume), C.byref(out), s),
            "aton_photon_sum_static")
     return out.value
+
+
+class Mlp:
+    """The chemistry-surrogate network (aton_mlp_*). Arrays are float32 torch CUDA tensors."""
+    NORM_LEN = 26
+
+    def __init__(self, seed=0):
+        self.L = load()
+        h = _VP()
+        _check(self.L.aton_mlp_create(C.byref(h), int(seed)), "aton_mlp_create")
+        self.h = h
+        self.n_params = self.L.aton_mlp_num_params()
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.aton_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta):
+        t = np.ascontiguousarray(theta, np.float32)
+        _check(self.L.aton_mlp_set_params(self.h, t.ctypes.data, HOST), "aton_mlp_set_params")
+
+    def get_params(self):
+        t = np.empty(self.n_params, np.float32)
+        _check(self.L.aton_mlp_get_params(self.h, t.ctypes.data, HOST), "aton_mlp_get_params")
+        return t
+
+    def fit_norm(self, records, dt):
+        _check(self.L.aton_mlp_fit_norm(self.h, records.data_ptr(), int(records.shape[0]),
+                                        float(dt)), "aton_mlp_fit_norm")
+
+    def get_norm(self):
+        v = np.empty(self.NORM_LEN, np.float32)
+        _check(self.L.aton_mlp_get_norm(self.h, v.ctypes.data), "aton_mlp_get_norm")
+        return v
+
+    def set_norm(self, v):
+        v = np.ascontiguousarray(v, np.float32)
+        _check(self.L.aton_mlp_set_norm(self.h, v.ctypes.data), "aton_mlp_set_norm")
+
+    def features(self, records, dt, targets=True):
+        import torch
+        n = int(records.shape[0])
+        X = torch.empty((n, 5), dtype=torch.float32, device=records.device)
+        T = torch.empty((n, 3), dtype=torch.float32, device=records.device) if targets else None
+        _check(self.L.aton_mlp_features(self.h, records.data_ptr(), n, float(dt), X.data_ptr(),
+                                        None if T is None else T.data_ptr()), "aton_mlp_features")
+        return X, T
+
+    def forward(self, X):
+        import torch
+        n = int(X.shape[0])
+        Y = torch.empty((n, 3), dtype=torch.float32, device=X.device)
+        _check(self.L.aton_mlp_forward(self.h, X.data_ptr(), n, Y.data_ptr()), "aton_mlp_forward")
+        return Y
+
+    def loss_grad(self, X, T):
+        import torch
+        g = torch.empty(self.n_params, dtype=torch.float32, device=X.device)
+        loss = C.c_double()
+        _check(self.L.aton_mlp_loss_grad(self.h, X.data_ptr(), T.data_ptr(), int(X.shape[0]),
+                                         g.data_ptr(), C.byref(loss)), "aton_mlp_loss_grad")
+        return loss.value, g
+
+    def train_step(self, X, T, lr, want_loss=False):
+        loss = C.c_double()
+        _check(self.L.aton_mlp_train_step(self.h, X.data_ptr(), T.data_ptr(), int(X.shape[0]),
+                                          float(lr), C.byref(loss) if want_loss else None),
+               "aton_mlp_train_step")
+        return loss.value if want_loss else None
+
+    def synchronize(self):
+        _check(self.L.aton_mlp_synchronize(self.h), "aton_mlp_synchronize")
 
 
 def from_workload(state, src_idx, src_rate, run, **params):

@@ -61,12 +61,12 @@ struct aton_ctx {
   // reductions
   double* d_part = nullptr;
   double* d_out = nullptr;            // [4]: acc3 + stored
-  unsigned long long* d_u64 = nullptr;  // [4]
+  unsigned long long* d_u64 = nullptr;  // [5]
   unsigned int* d_bad = nullptr;
   Slots slots;
   // folded tallies (density units for the photon sums)
   double fold_acc[3] = {0, 0, 0};
-  unsigned long long fold_u[4] = {0, 0, 0, 0};
+  unsigned long long fold_u[5] = {0, 0, 0, 0, 0};
   double emitted = 0, stored0 = 0;
   double offs[ATON_BUDGET_LEN] = {0};
   int64_t steps = 0;
@@ -88,6 +88,14 @@ struct aton_ctx {
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
   TmaMaps tma[3];          // tile heights 4, 8, 16
   bool tma_ok[3] = {false, false, false};
+  // pair sink and surrogate
+  float* sink = nullptr;
+  long long sink_cap = 0, sink_steps = 0;
+  int sink_stride = 1;
+  aton_mlp_handle sur = nullptr;
+  aton_surrogate_params sur_p{};
+  int* sur_list = nullptr;
+  int* sur_count = nullptr;
 
   cudaStream_t stream() const { return user ? user : own; }
 };
@@ -126,12 +134,13 @@ static StepParams step_params(const aton_ctx* h) {
 }
 
 static int slots_needed(const aton_ctx* h) {
-  return std::max(fused_tiles(h->nx, h->ny, h->nz, h->ty, h->tz), kPlainBlocks);
+  // the plain path with the surrogate uses two slot ranges of kPlainBlocks
+  return std::max(fused_tiles(h->nx, h->ny, h->nz, h->ty, h->tz), 2 * kPlainBlocks);
 }
 
 static void free_slots(Slots& s) {
   cudaFree(s.acc); cudaFree(s.sub); cudaFree(s.mx); cudaFree(s.err); cudaFree(s.nan);
-  cudaFree(s.timeout);
+  cudaFree(s.timeout); cudaFree(s.sur);
   s = Slots{};
 }
 
@@ -143,7 +152,7 @@ static int fold_slots(aton_handle h) {
   cudaStream_t s = h->stream();
   CU(launch_reduce_slots(h->slots, h->d_out, h->d_u64, s));
   double a[3];
-  unsigned long long u[4];
+  unsigned long long u[5];
   CU(cudaMemcpyAsync(a, h->d_out, sizeof(a), cudaMemcpyDeviceToHost, s));
   CU(cudaMemcpyAsync(u, h->d_u64, sizeof(u), cudaMemcpyDeviceToHost, s));
   CU(cudaStreamSynchronize(s));
@@ -152,12 +161,14 @@ static int fold_slots(aton_handle h) {
   h->fold_u[1] = std::max(h->fold_u[1], u[1]);
   h->fold_u[2] += u[2];
   h->fold_u[3] += u[3];
+  h->fold_u[4] += u[4];
   const int n = h->slots.n;
   CU(cudaMemsetAsync(h->slots.acc, 0, sizeof(double) * 3 * n, s));
   CU(cudaMemsetAsync(h->slots.sub, 0, sizeof(unsigned long long) * n, s));
   CU(cudaMemsetAsync(h->slots.mx, 0, sizeof(unsigned int) * n, s));
   CU(cudaMemsetAsync(h->slots.err, 0, sizeof(unsigned int) * n, s));
   CU(cudaMemsetAsync(h->slots.nan, 0, sizeof(unsigned int) * n, s));
+  CU(cudaMemsetAsync(h->slots.sur, 0, sizeof(unsigned int) * n, s));
   return ATON_OK;
 }
 
@@ -174,6 +185,7 @@ static int ensure_slots_n(aton_handle h, int need) {
   CU(cudaMalloc(&s.err, sizeof(unsigned int) * need));
   CU(cudaMalloc(&s.nan, sizeof(unsigned int) * need));
   CU(cudaMalloc(&s.timeout, sizeof(unsigned int)));
+  CU(cudaMalloc(&s.sur, sizeof(unsigned int) * need));
   s.n = need;
   h->slots = s;
   cudaStream_t st = h->stream();
@@ -183,6 +195,7 @@ static int ensure_slots_n(aton_handle h, int need) {
   CU(cudaMemsetAsync(s.err, 0, sizeof(unsigned int) * need, st));
   CU(cudaMemsetAsync(s.nan, 0, sizeof(unsigned int) * need, st));
   CU(cudaMemsetAsync(s.timeout, 0, sizeof(unsigned int), st));
+  CU(cudaMemsetAsync(s.sur, 0, sizeof(unsigned int) * need, st));
   return ATON_OK;
 }
 
@@ -269,7 +282,8 @@ static int enqueue_step(aton_handle h, cudaStream_t s) {
   const Fields in{h->f[h->cur][0], h->f[h->cur][1], h->f[h->cur][2], h->f[h->cur][3]};
   const Fields out{h->f[nxt][0], h->f[nxt][1], h->f[nxt][2], h->f[nxt][3]};
   cudaError_t e;
-  if (h->mode == ATON_MODE_FUSED || h->mode == ATON_MODE_FUSED_LDG) {
+  const bool plain_only = h->sink != nullptr || (h->sur && h->sur_p.enabled);
+  if (!plain_only && (h->mode == ATON_MODE_FUSED || h->mode == ATON_MODE_FUSED_LDG)) {
     FusedArgs a{};
     a.P = step_params(h);
     a.in = in; a.out = out;
@@ -288,7 +302,24 @@ static int enqueue_step(aton_handle h, cudaStream_t s) {
     a.y = h->y; a.T = h->T; a.nH = h->nH;
     a.src_idx = h->d_src_idx; a.src_dN = h->d_src_dN; a.nsrc = h->src_n;
     a.slots = h->slots;
+    if (h->sink) {
+      const long long per = (h->ncell + h->sink_stride - 1) / h->sink_stride;
+      a.sink = h->sink;
+      a.sink_cap = h->sink_cap;
+      a.sink_stride = h->sink_stride;
+      a.sink_phase = (int)(h->sink_steps % h->sink_stride);
+      a.sink_base = h->sink_steps * per;
+    }
+    if (h->sur && h->sur_p.enabled) {
+      a.sur_img = mlp_image(h->sur);
+      a.sur_norm = mlp_norm(h->sur);
+      a.sur_gate = (float)h->sur_p.gate_substeps;
+      a.sur_resid = (float)h->sur_p.residual_max;
+      a.sur_list = h->sur_list;
+      a.sur_count = h->sur_count;
+    }
     e = launch_plain_step(a, s);
+    if (h->sink) h->sink_steps += 1;
   }
   if (e != cudaSuccess) return fail(ATON_ERR_CUDA, "step launch: %s", cudaGetErrorString(e));
   h->cur = nxt;
@@ -350,6 +381,7 @@ void aton_finalize(aton_handle h) {
   cudaFree(h->d_part); cudaFree(h->d_out); cudaFree(h->d_u64); cudaFree(h->d_bad);
   free_slots(h->slots);
   cudaFree(h->d_src_idx); cudaFree(h->d_src_dN); cudaFree(h->d_tstart); cudaFree(h->d_tsrc);
+  cudaFree(h->sur_list); cudaFree(h->sur_count);
   if (h->own) cudaStreamDestroy(h->own);
   delete h;
 }
@@ -400,7 +432,7 @@ int aton_init(int nx, int ny, int nz, double dx_cm, double c_cms, double dt_s, a
     return bail(fail(ATON_ERR_NOMEM, "cudaMalloc of %zu bytes failed", fb));
   if (cudaMalloc(&h->d_part, sizeof(double) * kSumBlocks) != cudaSuccess ||
       cudaMalloc(&h->d_out, sizeof(double) * 4) != cudaSuccess ||
-      cudaMalloc(&h->d_u64, sizeof(unsigned long long) * 4) != cudaSuccess ||
+      cudaMalloc(&h->d_u64, sizeof(unsigned long long) * 5) != cudaSuccess ||
       cudaMalloc(&h->d_bad, sizeof(unsigned int)) != cudaSuccess)
     return bail(fail(ATON_ERR_NOMEM, "cudaMalloc of reduction scratch failed"));
   h->tz = std::min(64, nz);
@@ -519,6 +551,7 @@ int aton_set_fields(aton_handle h, const float* N, const float* Fx, const float*
   }
   std::memset(h->fold_acc, 0, sizeof(h->fold_acc));
   std::memset(h->fold_u, 0, sizeof(h->fold_u));
+  h->sink_steps = 0;
   std::memset(h->offs, 0, sizeof(h->offs));
   h->emitted = 0;
   h->steps = 0;
@@ -577,8 +610,9 @@ int aton_step(aton_handle h, int nsteps) {
   cudaStream_t s = h->stream();
   int left = nsteps;
   while (left > 0) {
-    const int b = h->graph_batch > 0 ? std::min(left, h->graph_batch) : 1;
-    if (h->graph_batch > 0) {
+    const bool graphs = h->graph_batch > 0 && h->sink == nullptr;
+    const int b = graphs ? std::min(left, h->graph_batch) : 1;
+    if (graphs) {
       auto key = std::make_pair(b, h->cur);
       auto it = h->graphs.find(key);
       if (it == h->graphs.end()) {
@@ -609,10 +643,10 @@ int aton_step(aton_handle h, int nsteps) {
   return ATON_OK;
 }
 
-static int read_tallies(aton_handle h, double acc[3], unsigned long long u[4], double* stored) {
+static int read_tallies(aton_handle h, double acc[3], unsigned long long u[5], double* stored) {
   cudaStream_t s = h->stream();
   double a[4] = {0, 0, 0, 0};
-  unsigned long long uu[4] = {0, 0, 0, 0};
+  unsigned long long uu[5] = {0, 0, 0, 0, 0};
   if (h->slots.n) {
     CU(launch_reduce_slots(h->slots, h->d_out, h->d_u64, s));
   }
@@ -626,12 +660,13 @@ static int read_tallies(aton_handle h, double acc[3], unsigned long long u[4], d
     h->latched = ATON_ERR_CUDA;
     return fail(ATON_ERR_CUDA, "%u CTAs gave up waiting on a pipeline barrier", tmo);
   }
-  if (!h->slots.n) { a[0] = a[1] = a[2] = 0; uu[0] = uu[1] = uu[2] = uu[3] = 0; }
+  if (!h->slots.n) { a[0] = a[1] = a[2] = 0; uu[0] = uu[1] = uu[2] = uu[3] = uu[4] = 0; }
   for (int i = 0; i < 3; ++i) acc[i] = h->fold_acc[i] + a[i];
   u[0] = h->fold_u[0] + uu[0];
   u[1] = std::max(h->fold_u[1], uu[1]);
   u[2] = h->fold_u[2] + uu[2];
   u[3] = h->fold_u[3] + uu[3];
+  u[4] = h->fold_u[4] + uu[4];
   if (stored) *stored = a[3];
   if (u[3]) h->latched = ATON_ERR_NONFINITE;
   else if (u[2]) h->latched = ATON_ERR_SUBCYCLE;
@@ -643,7 +678,7 @@ int aton_synchronize(aton_handle h) {
   CU(cudaStreamSynchronize(h->stream()));
   if (!h->fields_set) return ATON_OK;
   double acc[3];
-  unsigned long long u[4];
+  unsigned long long u[5];
   if (int rc = read_tallies(h, acc, u, nullptr)) return rc;
   return h->latched;
 }
@@ -653,7 +688,7 @@ int aton_photon_budget(aton_handle h, double* out) {
   if (!out) return fail(ATON_ERR_BADARG, "out is NULL");
   if (!h->fields_set) return fail(ATON_ERR_STATE, "aton_set_fields has not been called");
   double acc[3], st = 0;
-  unsigned long long u[4];
+  unsigned long long u[5];
   if (int rc = read_tallies(h, acc, u, &st)) return rc;
   out[ATON_B_EMITTED] = h->emitted + h->offs[ATON_B_EMITTED];
   out[ATON_B_STORED] = st * h->V;
@@ -680,9 +715,10 @@ int aton_get_diag(aton_handle h, aton_diag* out) {
   if (!out) return fail(ATON_ERR_BADARG, "out is NULL");
   if (!h->fields_set) return fail(ATON_ERR_STATE, "aton_set_fields has not been called");
   double acc[3];
-  unsigned long long u[4];
+  unsigned long long u[5];
   if (int rc = read_tallies(h, acc, u, nullptr)) return rc;
   out->steps = h->steps;
+  out->surrogate_cells = (int64_t)u[4];
   out->substeps_total = (int64_t)u[0];
   out->substeps_max = (int64_t)u[1];
   out->error_cells = (int64_t)u[2];
@@ -704,6 +740,52 @@ int aton_launches_per_step(aton_handle h, int* launches) {
   if (!launches) return fail(ATON_ERR_BADARG, "launches is NULL");
   if (h->mode == ATON_MODE_FUSED || h->mode == ATON_MODE_FUSED_LDG) *launches = 1;
   else *launches = h->src_n > 0 ? plain_launches() : plain_launches() - 1;
+  if ((h->sink || (h->sur && h->sur_p.enabled)) && *launches == 1)
+    *launches = h->src_n > 0 ? plain_launches() : plain_launches() - 1;
+  if (h->sur && h->sur_p.enabled) *launches += 1;   // the candidate pass (plus a counter reset)
+  return ATON_OK;
+}
+
+int aton_set_pair_sink(aton_handle h, float* records, int64_t capacity, int stride) {
+  if (int rc = check_h(h)) return rc;
+  if (records && (capacity < 1 || stride < 1))
+    return fail(ATON_ERR_BADARG, "capacity and stride must be >= 1");
+  h->sink = records;
+  h->sink_cap = records ? capacity : 0;
+  h->sink_stride = records ? stride : 1;
+  h->sink_steps = 0;
+  drop_graphs(h);
+  return ATON_OK;
+}
+
+int aton_pair_count(aton_handle h, int64_t* count) {
+  if (int rc = check_h(h)) return rc;
+  if (!count) return fail(ATON_ERR_BADARG, "count is NULL");
+  const long long per = (h->ncell + h->sink_stride - 1) / h->sink_stride;
+  *count = h->sink ? std::min<long long>(h->sink_steps * per, h->sink_cap) : 0;
+  return ATON_OK;
+}
+
+void aton_default_surrogate_params(aton_surrogate_params* p) {
+  if (!p) return;
+  p->enabled = 1;
+  p->gate_substeps = 8.0;
+  p->residual_max = 1e-4;
+}
+
+int aton_set_surrogate(aton_handle h, aton_mlp_handle m, const aton_surrogate_params* p) {
+  if (int rc = check_h(h)) return rc;
+  if (m && !p) return fail(ATON_ERR_BADARG, "params is NULL");
+  if (p && (!(p->gate_substeps >= 0) || !(p->residual_max >= 0)))
+    return fail(ATON_ERR_BADARG, "gate and residual must be >= 0");
+  if (m && p->enabled && !h->sur_list) {
+    CU(cudaMalloc(&h->sur_list, sizeof(int) * (size_t)h->ncell));
+    CU(cudaMalloc(&h->sur_count, sizeof(int)));
+  }
+  h->sur = m;
+  if (p) h->sur_p = *p;
+  else h->sur_p = aton_surrogate_params{};
+  drop_graphs(h);
   return ATON_OK;
 }
 

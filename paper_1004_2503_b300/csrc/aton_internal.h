@@ -11,12 +11,14 @@
 
 #include "aton.h"
 #include "aton_device.cuh"
+#include "aton_mlp.cuh"
 
 namespace aton {
 
 constexpr int kTileX = 32;          // cells per CTA row in x (one warp)
 constexpr int kPlainBlocks = 148 * 8;  // fixed grid of the unfused kernels (deterministic slots)
 constexpr int kPlainThreads = 256;
+constexpr int kSurBlocks = 148;        // grid of the surrogate pass (few candidate cells)
 
 // One point source of a fused tile: plane z, cell (tx + 32*ty) inside the tile, dN added.
 struct TileSrc {
@@ -34,6 +36,7 @@ struct Slots {
   unsigned int* err = nullptr;        // [n]: cells at the sub-cycle cap
   unsigned int* nan = nullptr;        // [n]: non-finite cells
   unsigned int* timeout = nullptr;    // [1]: pipeline waits that gave up (must stay 0)
+  unsigned int* sur = nullptr;        // [n]: cells whose chemistry the surrogate replaced
   int n = 0;
 };
 
@@ -73,6 +76,16 @@ struct PlainArgs {
   const float* src_dN;
   int nsrc;
   Slots slots;
+  // pair sink: every `sink_stride`-th cell (offset rotating with the step) writes a record
+  float* sink;
+  long long sink_cap, sink_base;
+  int sink_stride, sink_phase;
+  // surrogate chemistry
+  const MlpImage* sur_img;
+  const MlpNorm* sur_norm;
+  float sur_gate, sur_resid;
+  int* sur_list;        // candidate cells of the step (capacity ncell)
+  int* sur_count;       // number of candidates (reset before every chemistry pass)
 };
 
 // ---- last-failure message of the calling thread (aton_capi.cu) ----
@@ -87,6 +100,8 @@ bool make_tma_maps(int nx, int ny, int nz, int ty, float* const u[2][4], float* 
 cudaError_t launch_fused(int ty, const FusedArgs& a, cudaStream_t s);
 int fused_tiles(int nx, int ny, int nz, int ty, int tz);
 cudaError_t launch_plain_step(const PlainArgs& a, cudaStream_t s);
+const MlpImage* mlp_image(const struct ::aton_mlp* h);
+const MlpNorm* mlp_norm(const struct ::aton_mlp* h);
 int plain_launches();
 cudaError_t launch_scale(float* dst, const float* src, float k, int64_t n, cudaStream_t s);
 cudaError_t launch_one_minus(float* dst, const float* src, int64_t n, cudaStream_t s);

@@ -314,6 +314,19 @@ __global__ void k_plain_sources(const PlainArgs A) {
   if (s < A.nsrc) A.out.N[A.src_idx[s]] += A.src_dN[s];
 }
 
+// pair record of the chemistry operator: nH, N, y, T in; N', y', T' out; sub-steps
+__device__ __forceinline__ void sink_record(const PlainArgs& A, long long id, float n, float N0,
+                                            float y0, float T0, float N1, float y1, float T1,
+                                            int nsub) {
+  if (A.sink && (id + A.sink_phase) % A.sink_stride == 0) {
+    const long long r = A.sink_base + id / A.sink_stride;
+    if (r < A.sink_cap) {
+      float* o = A.sink + r * 8;
+      o[0] = n; o[1] = N0; o[2] = y0; o[3] = T0; o[4] = N1; o[5] = y1; o[6] = T1; o[7] = (float)nsub;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kPlainThreads) k_plain_chem(const PlainArgs A) {
   const StepParams& P = A.P;
   const long long ncell = (long long)P.nx * P.ny * P.nz;
@@ -323,6 +336,51 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain_chem(const PlainArgs A)
     float N = A.out.N[id], X = A.out.Fx[id] * P.rc, Y = A.out.Fy[id] * P.rc, Z = A.out.Fz[id] * P.rc;
     float y = A.y[id], T = A.T[id];
     const float n = __ldg(A.nH + id);
+    const float N0 = N, y0 = y, T0 = T;
+    const ChemOut co = chem_cell(P, n, N, X, Y, Z, y, T);
+    sink_record(A, id, n, N0, y0, T0, N, y, T, co.nsub);
+    tl.absorbed.add(N0 - N);
+    tl.sub += co.nsub;
+    tl.mx = max(tl.mx, (unsigned)co.nsub);
+    tl.err += co.err;
+    if (!isfinite(N) || !isfinite(T) || !isfinite(X + Y + Z)) tl.nan += 1;
+    A.out.N[id] = N; A.out.Fx[id] = X * P.c; A.out.Fy[id] = Y * P.c; A.out.Fz[id] = Z * P.c;
+    A.y[id] = y; A.T[id] = T;
+  }
+  flush_tally<kPlainThreads / 32>(tl, A.slots, blockIdx.x);
+}
+
+// Chemistry with the learned surrogate, pass 1: the exact operator for every cell except the
+// candidates, which are appended to a list. A cell is a candidate when the exact operator would
+// sub-cycle heavily -- the explicit estimate of the sub-step count from photo-ionisation
+// (Gamma y dt over eps max(y, y_floor)) and photo-heating (over eps T) is at least sur_gate --
+// and its features lie inside the training range. (The network's registers stay out of this
+// kernel, which keeps the occupancy of the plain chemistry kernel.)
+__global__ void __launch_bounds__(kPlainThreads) k_plain_chem_gate(const PlainArgs A) {
+  const StepParams& P = A.P;
+  const long long ncell = (long long)P.nx * P.ny * P.nz;
+  const float l10dt = log10f(P.dt);
+  Tally tl;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < ncell;
+       id += (long long)gridDim.x * blockDim.x) {
+    float N = A.out.N[id];
+    float y = A.y[id], T = A.T[id];
+    const float n = __ldg(A.nH + id);
+    const float Gam = P.csig * N;
+    const float ny = Gam * y * P.dt / (P.sub_eps * fmaxf(y, P.y_floor));
+    const float nT = P.fixed_T ? 0.f : Gam * y * P.eheat_K * P.dt / (P.sub_eps * T * 1.5f * (2.f - y));
+    if (fmaxf(ny, nT) >= A.sur_gate) {
+      const MlpNorm& nm = *A.sur_norm;
+      const float f[kMlpIn] = {log10f(n), log10f(fmaxf(y, 1e-10f)), log10f(T), log10f(fmaxf(N, 1e-30f)), l10dt};
+      bool inr = true;
+#pragma unroll
+      for (int i = 0; i < kMlpIn; ++i) inr = inr && f[i] >= nm.in_min[i] && f[i] <= nm.in_max[i];
+      if (inr) {
+        A.sur_list[atomicAdd(A.sur_count, 1)] = (int)id;
+        continue;
+      }
+    }
+    float X = A.out.Fx[id] * P.rc, Y = A.out.Fy[id] * P.rc, Z = A.out.Fz[id] * P.rc;
     const float N0 = N;
     const ChemOut co = chem_cell(P, n, N, X, Y, Z, y, T);
     tl.absorbed.add(N0 - N);
@@ -334,6 +392,100 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain_chem(const PlainArgs A)
     A.y[id] = y; A.T[id] = T;
   }
   flush_tally<kPlainThreads / 32>(tl, A.slots, blockIdx.x);
+}
+
+// Pass 2: the listed candidates, 32 per warp. The warp runs the MLP for its 32 cells on tensor
+// cores; a prediction is accepted only if its photons absorbed per atom, (N - N')/nH, match
+// the atoms ionised, (y - y') plus the recombinations over dt at the mean state, within
+// sur_resid of max(y, 1e-8); rejected cells take the exact operator. Tallies go to the slots
+// after the first pass's.
+__global__ void __launch_bounds__(kPlainThreads) k_plain_chem_sur(const PlainArgs A) {
+  __shared__ __align__(16) MlpImage W;
+  __shared__ float xs[kPlainThreads / 32][32][8];
+  __shared__ float ys[kPlainThreads / 32][32][4];
+  const int count = *A.sur_count;
+  Tally tl;
+  // blocks without a chunk of candidates skip the weight copy
+  if (blockIdx.x * (kPlainThreads / 32) < (count + 31) / 32) {
+    {
+      const uint4* s = reinterpret_cast<const uint4*>(A.sur_img);
+      uint4* d = reinterpret_cast<uint4*>(&W);
+      const int nb = (int)(offsetof(MlpImage, W2T) / 16);
+      for (int i = threadIdx.x; i < nb; i += blockDim.x) d[i] = s[i];
+      for (int i = threadIdx.x; i < 2 * kMlpH + 8; i += blockDim.x) W.b1[i] = A.sur_img->b1[i];
+    }
+    __syncthreads();
+    const MlpNorm nm = *A.sur_norm;
+    const StepParams& P = A.P;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const float l10dt = log10f(P.dt);
+    const int nchunk = (count + 31) / 32;
+    for (int ch = blockIdx.x * (kPlainThreads / 32) + w; ch < nchunk; ch += gridDim.x * (kPlainThreads / 32)) {
+      const int k = ch * 32 + lane;
+      const bool valid = k < count;
+      const long long id = valid ? A.sur_list[k] : 0;
+      float N = 0.f, X = 0.f, Y = 0.f, Z = 0.f, y = 1.f, T = 1e4f, n = 1.f;
+      if (valid) {
+        N = A.out.N[id]; X = A.out.Fx[id] * P.rc; Y = A.out.Fy[id] * P.rc; Z = A.out.Fz[id] * P.rc;
+        y = A.y[id]; T = A.T[id]; n = __ldg(A.nH + id);
+      }
+      const float N0 = N;
+      const float f[kMlpIn] = {log10f(n), log10f(fmaxf(y, 1e-10f)), log10f(T), log10f(fmaxf(N, 1e-30f)), l10dt};
+#pragma unroll
+      for (int i = 0; i < kMlpIn; ++i) xs[w][lane][i] = (f[i] - nm.in_mean[i]) * nm.in_scale[i];
+      __syncwarp();
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int r0 = half * 16;
+        const float* xa = xs[w][r0 + g];
+        const float* xb = xs[w][r0 + g + 8];
+        const unsigned a[4] = {pack_bf16(2 * t < kMlpIn ? xa[2 * t] : 0.f, 2 * t + 1 < kMlpIn ? xa[2 * t + 1] : 0.f),
+                               pack_bf16(2 * t < kMlpIn ? xb[2 * t] : 0.f, 2 * t + 1 < kMlpIn ? xb[2 * t + 1] : 0.f),
+                               0u, 0u};
+        float z1[8][4], z2[8][4], yo[4];
+        mlp_forward16<false>(W, a, z1, z2, yo);
+        if (2 * t < 4) {
+          ys[w][r0 + g][2 * t] = yo[0]; ys[w][r0 + g][2 * t + 1] = yo[1];
+          ys[w][r0 + g + 8][2 * t] = yo[2]; ys[w][r0 + g + 8][2 * t + 1] = yo[3];
+        }
+      }
+      __syncwarp();
+      bool done = false;
+      if (valid) {
+        const float dly = fminf(fmaxf(nm.out_mean[0] + ys[w][lane][0] / nm.out_scale[0], -kDlyMax), kDlyMax);
+        const float dlT = fminf(fmaxf(nm.out_mean[1] + ys[w][lane][1] / nm.out_scale[1], -kDlTMax), kDlTMax);
+        const float dlN = fminf(fmaxf(nm.out_mean[2] + ys[w][lane][2] / nm.out_scale[2], -kDlNMax), 0.f);
+        const float y1 = fminf(fmaxf(fmaxf(y, 1e-10f) * exp2f(3.321928f * dly), 0.f), 1.f);
+        const float T1 = fmaxf(T * exp2f(3.321928f * dlT), P.T_floor);
+        const float N1 = fminf(fmaxf(N, 1e-30f) * exp2f(3.321928f * dlN), N);
+        // photon-conservation residual
+        const float xm = 1.f - 0.5f * (y + y1);
+        const float am = alpha_B(kLog2TwoTHI - log2f(0.5f * (T + T1)));
+        const float rec = am * n * xm * xm * P.dt;
+        const float r = fabsf((N - N1) / n - ((y - y1) + rec)) / fmaxf(y, 1e-8f);
+        if (r <= A.sur_resid && isfinite(y1) && isfinite(T1) && isfinite(N1)) {
+          const float fr = N > 0.f ? N1 / N : 1.f;
+          N = N1; X *= fr; Y *= fr; Z *= fr; y = y1; T = T1;
+          done = true;
+          tl.sur += 1;
+        }
+        int nsub = 0;
+        if (!done) {
+          const ChemOut co = chem_cell(P, n, N, X, Y, Z, y, T);
+          nsub = co.nsub;
+          tl.err += co.err;
+        }
+        tl.absorbed.add(N0 - N);
+        tl.sub += nsub;
+        tl.mx = max(tl.mx, (unsigned)nsub);
+        if (!isfinite(N) || !isfinite(T) || !isfinite(X + Y + Z)) tl.nan += 1;
+        A.out.N[id] = N; A.out.Fx[id] = X * P.c; A.out.Fy[id] = Y * P.c; A.out.Fz[id] = Z * P.c;
+        A.y[id] = y; A.T[id] = T;
+      }
+      __syncwarp();
+    }
+  }
+  flush_tally<kPlainThreads / 32>(tl, A.slots, kPlainBlocks + blockIdx.x);
 }
 
 int plain_launches() { return 3; }
@@ -348,7 +500,16 @@ cudaError_t launch_plain_step(const PlainArgs& a, cudaStream_t s) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  k_plain_chem<<<kPlainBlocks, kPlainThreads, 0, s>>>(a);
+  if (a.sur_img) {
+    e = cudaMemsetAsync(a.sur_count, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_plain_chem_gate<<<kPlainBlocks, kPlainThreads, 0, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_plain_chem_sur<<<kSurBlocks, kPlainThreads, 0, s>>>(a);
+  } else {
+    k_plain_chem<<<kPlainBlocks, kPlainThreads, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -402,30 +563,31 @@ __global__ void __launch_bounds__(512) k_reduce_slots(const Slots S, double* out
                                                       unsigned long long* out4) {
   constexpr int NT = 512;
   __shared__ double sa[3][NT];
-  __shared__ unsigned long long su[4][NT];
+  __shared__ unsigned long long su[5][NT];
   const int t = threadIdx.x;
   double a0 = 0, a1 = 0, a2 = 0;
-  unsigned long long sb = 0, mx = 0, er = 0, na = 0;
+  unsigned long long sb = 0, mx = 0, er = 0, na = 0, us = 0;
   for (int i = t; i < S.n; i += NT) {
     a0 += S.acc[3 * i]; a1 += S.acc[3 * i + 1]; a2 += S.acc[3 * i + 2];
     sb += S.sub[i];
     mx = max(mx, (unsigned long long)S.mx[i]);
-    er += S.err[i]; na += S.nan[i];
+    er += S.err[i]; na += S.nan[i]; us += S.sur[i];
   }
   sa[0][t] = a0; sa[1][t] = a1; sa[2][t] = a2;
-  su[0][t] = sb; su[1][t] = mx; su[2][t] = er; su[3][t] = na;
+  su[0][t] = sb; su[1][t] = mx; su[2][t] = er; su[3][t] = na; su[4][t] = us;
   __syncthreads();
   for (int w = NT / 2; w > 0; w >>= 1) {
     if (t < w) {
       sa[0][t] += sa[0][t + w]; sa[1][t] += sa[1][t + w]; sa[2][t] += sa[2][t + w];
       su[0][t] += su[0][t + w]; su[1][t] = max(su[1][t], su[1][t + w]);
-      su[2][t] += su[2][t + w]; su[3][t] += su[3][t + w];
+      su[2][t] += su[2][t + w]; su[3][t] += su[3][t + w]; su[4][t] += su[4][t + w];
     }
     __syncthreads();
   }
   if (t == 0) {
     out_acc3[0] = sa[0][0]; out_acc3[1] = sa[1][0]; out_acc3[2] = sa[2][0];
     out4[0] = su[0][0]; out4[1] = su[1][0]; out4[2] = su[2][0]; out4[3] = su[3][0];
+    out4[4] = su[4][0];
   }
 }
 
