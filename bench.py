@@ -136,6 +136,59 @@ def time_oracle(cst, cidx, crate, crun, steps, omp=False):
     return cst["N"].size * steps / dt, dt
 
 
+def surrogate_leg(args):
+    """Chemistry surrogate on the 256^3 lognormal workload: trained on pairs of the exact
+    operator from 64^3 boxes with disjoint seeds, then the plain step with and without it from
+    the same state (residual threshold 1e-4, gate 8 sub-steps)."""
+    import torch
+    from paper_1004_2503_b300 import aton as A
+    from paper_1004_2503_b300 import surrogate as S
+    from paper_1004_2503_b300 import workloads as W
+    t0 = time.perf_counter()
+    train_wl = [W.cosmo_box(64, 2.0, 48, s, s + 1000) for s in range(100, 112)]
+    rec = S.collect_pairs(train_wl, steps=120, stride=1, capacity=40_000_000, keep_light=0.01)
+    m = A.Mlp(seed=11)
+    S.train(m, rec, train_wl[0][3]["dt"], steps=3000, batch=16384)
+    t_train = time.perf_counter() - t0
+    st, idx, rate, run = W.workload_256()
+    out = {}
+    for name in ("exact", "surrogate"):
+        a = A.from_workload(st, idx, rate, run)
+        s = torch.cuda.Stream()
+        a.set_stream(s)
+        a.set_exec(A.MODE_UNFUSED, args.graph_batch)
+        if name == "surrogate":
+            a.set_surrogate(m, gate_substeps=8.0, residual_max=1e-4)
+        a.step(5)
+        a.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        k = 60
+        e0.record(s)
+        a.step(k)
+        e1.record(s)
+        e1.synchronize()
+        f = a.get_fields()
+        b = a.photon_budget()
+        d = a.diag()
+        a.close()
+        out[name] = dict(ms=e0.elapsed_time(e1) / k, x=f["x"], d=d,
+                         clos=(b["stored0"] + b["emitted"] - b["stored"] - b["absorbed"] -
+                               b["escaped"] - b["clipped"]) / b["emitted"])
+    m.close()
+    ion = lambda f: float(np.sum(st["nH"] * f))   # noqa: E731
+    ex, su = out["exact"], out["surrogate"]
+    return {"workload": "lognormal 256^3 (sigma_ln=2.0, 1024 sources), plain step, 60 steps",
+            "ms_per_step_exact": ex["ms"], "ms_per_step_surrogate": su["ms"],
+            "speedup": ex["ms"] / su["ms"],
+            "surrogate_cells_per_step": su["d"]["surrogate_cells"] / su["d"]["steps"],
+            "heavy_substeps_per_cell_exact": ex["d"]["substeps_total"] / (ex["d"]["steps"] * st["N"].size),
+            "ionised_atoms_rel_err": ion(su["x"]) / ion(ex["x"]) - 1,
+            "max_abs_dx": float(np.abs(su["x"] - ex["x"]).max()),
+            "budget_closure": su["clos"], "residual_max": 1e-4, "gate_substeps": 8.0,
+            "train_records": int(rec.shape[0]), "train_seconds": t_train}
+
+
 def reference_arm(args, world, rank):
     if rank != 0:
         return
@@ -313,6 +366,8 @@ def finish(args, world, rank, dist, st, idx, rate, run, desc, ncell, value, ms, 
         "budget_closure": (bud["stored0"] + bud["emitted"] - bud["stored"] - bud["absorbed"] -
                            bud["escaped"] - bud["clipped"]) / max(bud["emitted"], 1e-300),
     }
+    if rank == 0 and not args.no_surrogate:
+        line["surrogate"] = surrogate_leg(args)
     if rank == 0 and not args.no_cpu:
         cst, cidx, crate, crun, side, org = cpu_sample(st, idx, rate, run, 2.5e6)
         v1, d1 = time_oracle(cst, cidx, crate, crun, 4)
@@ -339,6 +394,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-unfused", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--tile", default="", help="TY,TZ of the fused kernel (skips the autotuner)")
     ap.add_argument("--kernel", default="tma", choices=["tma", "ldg"],
                     help="fused kernel used with --tile (the autotuner chooses otherwise)")
