@@ -37,7 +37,7 @@ NCU_TRAFFIC = {}
 
 def kernel_hash():
     h = hashlib.sha1()
-    for f in ("aton_kernels.cu", "aton_device.cuh"):
+    for f in ("aton_kernels.cu", "aton_tma.cu", "aton_device.cuh", "aton_step_common.cuh"):
         with open(os.path.join(ROOT, "paper_1004_2503_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]

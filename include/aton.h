@@ -153,7 +153,8 @@ int aton_autotune(aton_handle h, int steps, int* ty_out, int* tz_out, float* ms_
  * (converted y = 1 - x on the device); exactly one of x, y must be non-NULL.
  * Resets the photon budget and the counters; stored0 becomes sum N V.
  * Errors: BADARG (NULL pointers, both/neither of x,y, bad where), NONFINITE (a non-finite or
- * negative N, T <= 0, nH <= 0, y outside [0,1]: checked on the device), CUDA. */
+ * negative N, T <= 0, nH not a positive normal float (below 1.18e-38), y outside [0,1]:
+ * checked on the device), CUDA. */
 int aton_set_fields(aton_handle h, const float* N, const float* Fx, const float* Fy,
                     const float* Fz, const float* x, const float* y, const float* T,
                     const float* nH, int where);

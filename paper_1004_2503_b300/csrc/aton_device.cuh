@@ -44,10 +44,19 @@ struct ND6 {
 // along Fh, as D = n (x) n requires.
 constexpr float kNTiny = 1e-30f;
 
+// Hardware reciprocal and quotient (a couple of ulp). Used only where the divisor is a
+// positive normal FP32 number well inside the range (every call site states why).
+__device__ __forceinline__ float rcp_fast(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float div_fast(float a, float b) { return __fdividef(a, b); }
+
 __device__ __forceinline__ ND6 m1_pressure(float N, float fx, float fy, float fz) {
   ND6 r;
   if (N > kNTiny) {
-    const float rN = 1.f / N;
+    const float rN = rcp_fast(N);   // N in (1e-30, 8e37): the reciprocal stays normal
     float gx = fx * rN, gy = fy * rN, gz = fz * rN;
     float f2 = gx * gx + gy * gy + gz * gz;
     if (f2 > 1.f) {
@@ -55,14 +64,14 @@ __device__ __forceinline__ ND6 m1_pressure(float N, float fx, float fy, float fz
       gx *= k; gy *= k; gz *= k;
       f2 = 1.f;
     }
-    const float s = sqrtf(4.f - 3.f * f2);
-    const float r5 = 1.f / (5.f + 2.f * s);
-    const float iso = (1.f + s - 2.f * f2) * r5 * N;
-    const float Nc2 = 3.f * (2.f + 1.f / (2.f + s)) * r5 * N;
+    const float s = sqrtf(4.f - 3.f * f2);        // in [1, 2]
+    const float r5N = rcp_fast(5.f + 2.f * s) * N;
+    const float iso = (1.f + s - 2.f * f2) * r5N;
+    const float Nc2 = fmaf(3.f, rcp_fast(2.f + s), 6.f) * r5N;
     const float ax = Nc2 * gx, ay = Nc2 * gy;
-    r.xx = iso + ax * gx;
-    r.yy = iso + ay * gy;
-    r.zz = iso + Nc2 * gz * gz;
+    r.xx = fmaf(ax, gx, iso);
+    r.yy = fmaf(ay, gy, iso);
+    r.zz = fmaf(Nc2 * gz, gz, iso);
     r.xy = ax * gy;
     r.xz = ax * gz;
     r.yz = ay * gz;
@@ -104,17 +113,19 @@ __device__ __forceinline__ float beta_coll(float l, float l2T, float rT) {
 // net cooling per H atom / kB [K s^-1] at (T, x, y = 1 - x, nH), with recombination clumping CR
 __device__ __forceinline__ float cooling_K(float T, float l, float l2T, float rT, float x, float y,
                                            float n, float CR, bool coll_ion) {
-  // case-B recombination cooling (Hui & Gnedin 1997), times n_e n_HII
+  // case-B recombination cooling (Hui & Gnedin 1997), times n_e n_HII; the factor T enters the
+  // exponent as log2 T
   const float qr = exp2f(0.376f * (l - 1.169925001f));
-  const float rec = (float)(3.435e-30 / kKB) * T * exp2f(1.970f * l - 3.720f * log2f(1.f + qr));
-  // collisional excitation (Cen 1992), times n_e n_HI (exactly 0 in FP32 below kTExcMin)
-  const float ce = T > kTExcMin ? (float)(7.5e-19 / kKB) * exp2f(-(118348.f * kLog2e) * rT) /
-                                       (1.f + sqrtf(T * 1e-5f))
+  const float rec = (float)(3.435e-30 / kKB) * exp2f(1.970f * l + l2T - 3.720f * log2f(1.f + qr));
+  // collisional excitation (Cen 1992), times n_e n_HI (exactly 0 in FP32 below kTExcMin);
+  // the divisor is in [1, 1 + sqrt(T/1e5)]
+  const float ce = T > kTExcMin ? div_fast((float)(7.5e-19 / kKB) * exp2f(-(118348.f * kLog2e) * rT),
+                                           1.f + sqrtf(T * 1e-5f))
                                  : 0.f;
-  // bremsstrahlung with the Cen (1992) Gaunt factor, times n_e n_HII
+  // bremsstrahlung with the Cen (1992) Gaunt factor, times n_e n_HII; sqrt T = 2^(l2T / 2)
   const float d = l2T * kLog10of2 - 5.5f;
   const float gff = 1.1f + 0.34f * exp2f(-(kLog2e / 3.f) * d * d);
-  const float ff = (float)(1.42e-27 / kKB) * gff * sqrtf(T);
+  const float ff = (float)(1.42e-27 / kKB) * gff * exp2f(0.5f * l2T);
   float lx2 = CR * rec + ff;
   float lxy = ce;
   if (coll_ion && T > kTBetaMin) lxy += kTHI * beta_coll(l, l2T, rT);   // 13.6 eV each
@@ -146,6 +157,7 @@ __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float
   if (P.clR_A > 0.f) CR = fmaxf(1.f, P.clR_A * exp2f(P.clR_b * log2f(n)));
   if (P.clI_A > 0.f) CI = fmaxf(1.f, P.clI_A * exp2f(P.clI_b * log2f(n)));
   const float ksig = CI * P.csig;
+  const float CRn = CR * n;
   // Remaining time as an unevaluated float pair rh + rl (error-free TwoSum updates): a plain
   // FP32 "rem -= h" stalls once h < ulp(rem)/2 (about 4e3 s for dt ~ 1e11 s, while dense gas
   // can need sub-steps of 1e3 s), and rounding h to coarse ticks would change the sequence.
@@ -162,56 +174,63 @@ __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float
     const float rem = rh;
     const float xi = 1.f - yc;
     const float l2T = log2f(Tc);
-    const float rT = 1.f / Tc;
+    const float rT = rcp_fast(Tc);   // T_floor <= Tc < FP32 max (validated input, floored update)
     const float l = kLog2TwoTHI - l2T;
-    const float alpha = CR * alpha_B(l);
+    const float an = CRn * alpha_B(l);   // C_R alpha nH
     // the collisional rate is exactly 0 in FP32 below kTBetaMin, so it is not evaluated there
-    const float beta = (P.coll_ion && Tc > kTBetaMin) ? beta_coll(l, l2T, rT) : 0.f;
+    const float bn = (P.coll_ion && Tc > kTBetaMin) ? n * beta_coll(l, l2T, rT) : 0.f;
     const float Gam = ksig * Nc;
-    const float dydt = alpha * n * xi * xi - (Gam + beta * n * xi) * yc;
+    const float dydt = an * xi * xi - (Gam + bn * xi) * yc;
     float h = rem;
     const float ymax = fmaxf(yc, P.y_floor);
     const float ady = fabsf(dydt);
-    if (ady * h > P.sub_eps * ymax) h = P.sub_eps * ymax / ady;
+    // (the quotients below are taken only when the limit binds: the divisor is then positive
+    // and finite)
+    if (ady * h > P.sub_eps * ymax) h = div_fast(P.sub_eps * ymax, ady);
     float LK = 0.f;
     if (!P.fixed_T) {
       if (P.cooling) LK = cooling_K(Tc, l, l2T, rT, xi, yc, n, CR, P.coll_ion != 0);
-      // gross rate: heating and cooling each bounded (no cancellation near thermal balance)
+      // gross rate: heating and cooling each bounded (no cancellation near thermal balance);
+      // (heat + LK) / (1.5 (1 + x)) h <= eps T written without the quotient
       const float heat = Gam * yc * P.eheat_K;
-      const float rate = (heat + LK) / (1.5f * (1.f + xi));
+      const float gross = heat + LK;
+      const float cap = P.sub_eps * Tc * (1.5f * (1.f + xi));
       const bool pinned = Tc <= P.T_floor && heat < LK;   // cannot cool below the floor
-      if (!pinned && rate * h > P.sub_eps * Tc) h = P.sub_eps * Tc / rate;
+      if (!pinned && gross * h > cap) h = div_fast(cap, gross);
     }
     const bool last = !(h < rem);   // the last sub-step ends exactly at dt
-    const float a = h * alpha * n;
-    const float b = h * beta * n * xi;
+    const float a = h * an;
+    const float b = h * bn * xi;
     const float kk = ksig * h;
     const float m = n * kk;
     const float kN = kk * Nc;
     // Newton on the change d = y - y' (no cancellation in y' - y when the change is small):
     // g = -d - a (x + d)^2 + kN y'/(1 + m y') + b y', dg/dd = -(1 + 2a(x+d) + kN/(1+my')^2 + b)
+    // <= -1, |d2g/dd2| <= 2 (a + kN m). The iteration stops when the step just taken, or the
+    // next one predicted from it (at most (a + kN m) step^2), is below 3e-7 |d|.
+    const float Mq = a + kN * m;
     float d = 0.f;
     for (int it = 0; it < 40; ++it) {
       const float Yv = yc - d;
       const float omY = xi + d;
-      const float rd = 1.f / (1.f + m * Yv);
+      const float rd = rcp_fast(1.f + m * Yv);   // 1 + m y' >= 1
       const float kNr = kN * rd;
-      const float g = -d - a * omY * omY + kNr * Yv + b * Yv;
+      const float g = (kNr + b) * Yv - d - a * omY * omY;
       const float gp = 1.f + 2.f * a * omY + kNr * rd + b;
-      const float dn = fminf(fmaxf(d + g / gp, yc - 1.f), yc);
+      const float dn = fminf(fmaxf(d + div_fast(g, gp), yc - 1.f), yc);   // gp >= 1
       const float dd = fabsf(dn - d);
       d = dn;
-      if (dd <= 3e-7f * fabsf(d)) break;
+      if (fminf(Mq * dd, 1.f) * dd <= 3e-7f * fabsf(d)) break;
     }
     const float Y = yc - d;
     // photons absorbed in the sub-step: N r with r = m y'/(1 + m y'). N keeps full relative
     // precision either way: a large fraction is applied as N/(1 + m y') (no cancellation), a
     // small one (down to r << ulp(1)) is subtracted from the pair with an error-free TwoSum.
     const float mY = m * Y;
-    const float r = mY / (1.f + mY);
+    const float r = div_fast(mY, 1.f + mY);
     const float dN = Nc * r;
     if (r > 0.5f) {
-      Nh = Nc / (1.f + mY);
+      Nh = div_fast(Nc, 1.f + mY);
       Nl = 0.f;
     } else {
       const float sm = Nh - dN;
@@ -224,9 +243,10 @@ __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float
     Nh = fmaxf(Nh, 0.f);
     const float Nn = Nh + Nl;
     if (!P.fixed_T) {
-      const float num = 1.5f * (1.f + xi) * Tc + (dN / n) * P.eheat_K;
+      // den >= 1.5 and bounded by the sub-step rule
+      const float num = 1.5f * (1.f + xi) * Tc + div_fast(dN, n) * P.eheat_K;
       const float den = 1.5f * (2.f - Y) + h * LK * rT;
-      Tc = fmaxf(num / den, P.T_floor);
+      Tc = fmaxf(div_fast(num, den), P.T_floor);
     }
     Nc = Nn;
     yc = Y;
@@ -244,7 +264,7 @@ __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float
   }
   // F decays by the same factor as N in every sub-step, so by N_final / N_0 overall (after the
   // realisability clamp N = 0 implies F = 0)
-  const float fr = N0 > 0.f ? Nc / N0 : 1.f;
+  const float fr = N0 > 0.f ? div_fast(Nc, N0) : 1.f;
   N = Nc;
   fx *= fr;
   fy *= fr;

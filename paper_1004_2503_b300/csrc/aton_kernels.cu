@@ -27,9 +27,13 @@ namespace aton {
 // =========================================================================================
 template <int TY, bool PER>
 __global__ void __launch_bounds__(kTileX * TY) k_fused(const FusedArgs A) {
-  constexpr int TX = kTileX, PX = TX + 2, PL = PX * (TY + 2), NQ = 10;
+  constexpr int TX = kTileX, RX = kRingRX, PLR = RX * (TY + 2);
   constexpr int NH = 2 * TX + 2 * TY;
-  extern __shared__ float sm[];  // [3][NQ][PL]: N, Fx, Fy, Fz, Dxx, Dyy, Dzz, Dxy, Dxz, Dyz
+  // three-plane ring: [3][PLR] (N, F/c), [3][PLR] N (Dxx, Dxy, Dxz, Dyy), [3][PLR] N (Dyz, Dzz)
+  extern __shared__ float4 ring[];
+  float4* RU = ring;
+  float4* RA = RU + 3 * PLR;
+  float2* RB = reinterpret_cast<float2*>(RA + 3 * PLR);
   const StepParams& P = A.P;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
   const int nx = P.nx, ny = P.ny, nz = P.nz;
@@ -39,159 +43,95 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused(const FusedArgs A) {
   const int gx = x0 + tx, gy = y0 + ty;
   const bool act = (gx < nx) && (gy < ny);
   const long long ocol = bc_map(gx, nx, PER) + (long long)nx * bc_map(gy, ny, PER);
-  const int oslot = (ty + 1) * PX + (tx + 1);
+  const int oslot = (ty + 1) * RX + (tx + 1);
   int hslot = -1;
   long long hcol = 0;
-  if (tid < NH) {
+  if (tid < NH) {   // the halo ring of the tile: rows y0-1 and y0+TY, columns x0-1 and x0+TX
     int hx, hy;
     if (tid < TX) { hx = tid; hy = -1; }
     else if (tid < 2 * TX) { hx = tid - TX; hy = TY; }
     else if (tid < 2 * TX + TY) { hx = -1; hy = tid - 2 * TX; }
     else { hx = TX; hy = tid - 2 * TX - TY; }
-    hslot = (hy + 1) * PX + (hx + 1);
+    hslot = (hy + 1) * RX + (hx + 1);
     hcol = bc_map(x0 + hx, nx, PER) + (long long)nx * bc_map(y0 + hy, ny, PER);
   }
   const float* __restrict__ iN = A.in.N;
   const float* __restrict__ iX = A.in.Fx;
   const float* __restrict__ iY = A.in.Fy;
   const float* __restrict__ iZ = A.in.Fz;
-  const float rc = P.rc, cl = P.c;
+  const float rc = P.rc, lam = P.lam;
+  const float hl = 0.5f * lam, cu = 1.f - 3.f * lam;
   auto pz = [&](int z) { return (long long)bc_map(z, nz, PER) * plane; };
-  auto put = [&](float* S, int slot, const float u[4], const ND6& d) {
-    S[0 * PL + slot] = u[0]; S[1 * PL + slot] = u[1];
-    S[2 * PL + slot] = u[2]; S[3 * PL + slot] = u[3];
-    S[4 * PL + slot] = d.xx; S[5 * PL + slot] = d.yy; S[6 * PL + slot] = d.zz;
-    S[7 * PL + slot] = d.xy; S[8 * PL + slot] = d.xz; S[9 * PL + slot] = d.yz;
+  auto ld = [&](long long o) {
+    return make_float4(__ldg(iN + o), __ldg(iX + o) * rc, __ldg(iY + o) * rc, __ldg(iZ + o) * rc);
   };
 
-  float um[4], pm[4], uc[4], pc[4], nu[4], nh[4] = {0.f, 0.f, 0.f, 0.f};
-  // prologue: plane z0-1 (registers only) and plane z0 (ring slot 0)
-  {
-    const long long o = pz(z0 - 1) + ocol;
-    um[0] = __ldg(iN + o); um[1] = __ldg(iX + o) * rc; um[2] = __ldg(iY + o) * rc; um[3] = __ldg(iZ + o) * rc;
-    const ND6 d = m1_pressure(um[0], um[1], um[2], um[3]);
-    pm[0] = um[3]; pm[1] = d.xz; pm[2] = d.yz; pm[3] = d.zz;
-  }
-  {
-    const long long p0 = pz(z0);
-    const long long o = p0 + ocol;
-    uc[0] = __ldg(iN + o); uc[1] = __ldg(iX + o) * rc; uc[2] = __ldg(iY + o) * rc; uc[3] = __ldg(iZ + o) * rc;
-    const ND6 d = m1_pressure(uc[0], uc[1], uc[2], uc[3]);
-    pc[0] = uc[3]; pc[1] = d.xz; pc[2] = d.yz; pc[3] = d.zz;
-    put(sm, oslot, uc, d);
-    if (hslot >= 0) {
-      const long long oh = p0 + hcol;
-      float hu[4] = {__ldg(iN + oh), __ldg(iX + oh) * rc, __ldg(iY + oh) * rc, __ldg(iZ + oh) * rc};
-      put(sm, hslot, hu, m1_pressure(hu[0], hu[1], hu[2], hu[3]));
-    }
-  }
-  {
-    const long long p1 = pz(z0 + 1);
-    const long long o = p1 + ocol;
-    nu[0] = __ldg(iN + o); nu[1] = __ldg(iX + o) * rc; nu[2] = __ldg(iY + o) * rc; nu[3] = __ldg(iZ + o) * rc;
-    if (hslot >= 0) {
-      const long long oh = p1 + hcol;
-      nh[0] = __ldg(iN + oh); nh[1] = __ldg(iX + oh) * rc; nh[2] = __ldg(iY + oh) * rc; nh[3] = __ldg(iZ + oh) * rc;
-    }
-  }
+  // prologue: plane z0-1 (own column, registers), plane z0 (ring slot 0), plane z0+1 (registers)
+  float4 um = ld(pz(z0 - 1) + ocol);
+  float4 pm = z_flux(um);
+  float4 uc = ld(pz(z0) + ocol);
+  float4 pc = ring_put(RU, RA, RB, oslot, uc);
+  if (hslot >= 0) ring_put(RU, RA, RB, hslot, ld(pz(z0) + hcol));
+  float4 nu = ld(pz(z0 + 1) + ocol);
+  float4 nh = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (hslot >= 0) nh = ld(pz(z0 + 1) + hcol);
   float cy = 0.f, cT = 1.f, cn = 1.f;
-  if (act) {
-    const long long o = (long long)z0 * plane + ocol;
-    cy = A.y[o]; cT = A.T[o]; cn = __ldg(A.nH + o);
-  }
+  long long o = (long long)z0 * plane + ocol;
+  if (act) { cy = A.y[o]; cT = A.T[o]; cn = __ldg(A.nH + o); }
 
+  // the tile's next point source (host-merged, sorted by plane, at most one entry per cell)
   const int tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   int sp = A.tsrc_start[tile];
   const int se = A.tsrc_start[tile + 1];
+  TileSrc src{nz, 0, 0.f, 0};
+  if (sp < se) src = A.tsrc[sp];
   Tally tl;
-  const float lam = P.lam;
 
-  for (int z = z0; z < z1; ++z) {
-    const int bc = (z - z0) % 3, bn = (z - z0 + 1) % 3;
-    float* Sn = sm + bn * NQ * PL;
-    // plane z+1 into the ring (own cell and halo cell), z-flux of the own cell kept
-    float up[4] = {nu[0], nu[1], nu[2], nu[3]}, pp[4];
-    {
-      const ND6 d = m1_pressure(up[0], up[1], up[2], up[3]);
-      pp[0] = up[3]; pp[1] = d.xz; pp[2] = d.yz; pp[3] = d.zz;
-      put(Sn, oslot, up, d);
-      if (hslot >= 0) put(Sn, hslot, nh, m1_pressure(nh[0], nh[1], nh[2], nh[3]));
-    }
+  // offset of plane z+2 (boundary-mapped), advanced without an integer modulo
+  int zz2 = bc_map(z0 + 2, nz, PER);
+  long long p2 = (long long)zz2 * plane;
+  int rcur = 0;
+  for (int z = z0; z < z1; ++z, o += plane) {
+    const int rnx = rcur == 2 ? 0 : rcur + 1;
+    // plane z+1 into the ring (own and halo slot); its z flux kept in registers
+    const float4 up = nu;
+    const float4 pp = ring_put(RU + rnx * PLR, RA + rnx * PLR, RB + rnx * PLR, oslot, up);
+    if (hslot >= 0) ring_put(RU + rnx * PLR, RA + rnx * PLR, RB + rnx * PLR, hslot, nh);
     // prefetch plane z+2 and the chemistry fields of plane z+1
     float ny_ = 0.f, nT_ = 1.f, nn_ = 1.f;
     if (z + 1 < z1) {
-      const long long p2 = pz(z + 2);
-      const long long o = p2 + ocol;
-      nu[0] = __ldg(iN + o); nu[1] = __ldg(iX + o) * rc; nu[2] = __ldg(iY + o) * rc; nu[3] = __ldg(iZ + o) * rc;
-      if (hslot >= 0) {
-        const long long oh = p2 + hcol;
-        nh[0] = __ldg(iN + oh); nh[1] = __ldg(iX + oh) * rc; nh[2] = __ldg(iY + oh) * rc; nh[3] = __ldg(iZ + oh) * rc;
-      }
-      if (act) {
-        const long long oc = (long long)(z + 1) * plane + ocol;
-        ny_ = A.y[oc]; nT_ = A.T[oc]; nn_ = __ldg(A.nH + oc);
-      }
+      nu = ld(p2 + ocol);
+      if (hslot >= 0) nh = ld(p2 + hcol);
+      if (act) { ny_ = A.y[o + plane]; nT_ = A.T[o + plane]; nn_ = __ldg(A.nH + o + plane); }
     }
     __syncthreads();
     if (act) {
-      const float* S = sm + bc * NQ * PL;
-      const float* L = S + oslot - 1;
-      const float* R = S + oslot + 1;
-      const float* D = S + oslot - PX;
-      const float* U = S + oslot + PX;
-      const float c0 = 2.f * uc[0], c1 = 2.f * uc[1], c2 = 2.f * uc[2], c3 = 2.f * uc[3];
-      // x faces: flux (Fx, Dxx, Dxy, Dxz)
-      float aN = 0.5f * (R[1 * PL] - L[1 * PL]) - 0.5f * (R[0] - c0 + L[0]);
-      float aX = 0.5f * (R[4 * PL] - L[4 * PL]) - 0.5f * (R[1 * PL] - c1 + L[1 * PL]);
-      float aY = 0.5f * (R[7 * PL] - L[7 * PL]) - 0.5f * (R[2 * PL] - c2 + L[2 * PL]);
-      float aZ = 0.5f * (R[8 * PL] - L[8 * PL]) - 0.5f * (R[3 * PL] - c3 + L[3 * PL]);
-      // y faces: flux (Fy, Dxy, Dyy, Dyz)
-      aN += 0.5f * (U[2 * PL] - D[2 * PL]) - 0.5f * (U[0] - c0 + D[0]);
-      aX += 0.5f * (U[7 * PL] - D[7 * PL]) - 0.5f * (U[1 * PL] - c1 + D[1 * PL]);
-      aY += 0.5f * (U[5 * PL] - D[5 * PL]) - 0.5f * (U[2 * PL] - c2 + D[2 * PL]);
-      aZ += 0.5f * (U[9 * PL] - D[9 * PL]) - 0.5f * (U[3 * PL] - c3 + D[3 * PL]);
-      // z faces: flux (Fz, Dxz, Dyz, Dzz) from registers
-      aN += 0.5f * (pp[0] - pm[0]) - 0.5f * (up[0] - c0 + um[0]);
-      aX += 0.5f * (pp[1] - pm[1]) - 0.5f * (up[1] - c1 + um[1]);
-      aY += 0.5f * (pp[2] - pm[2]) - 0.5f * (up[2] - c2 + um[2]);
-      aZ += 0.5f * (pp[3] - pm[3]) - 0.5f * (up[3] - c3 + um[3]);
-      float Nn = uc[0] - lam * aN;
-      float Xn = uc[1] - lam * aX;
-      float Yn = uc[2] - lam * aY;
-      float Zn = uc[3] - lam * aZ;
+      const int c0 = rcur * PLR + oslot;
+      float4 u = lf_update(RU + c0, RA + c0, RB + c0, uc, um, pm, up, pp, cu, hl);
       if (!PER) {  // transmissive faces: outward photon flux through the boundary
         float e = 0.f;
-        if (gx == 0) e -= uc[1];
-        if (gx == nx - 1) e += uc[1];
-        if (gy == 0) e -= uc[2];
-        if (gy == ny - 1) e += uc[2];
-        if (z == 0) e -= uc[3];
-        if (z == nz - 1) e += uc[3];
+        if (gx == 0) e -= uc.y;
+        if (gx == nx - 1) e += uc.y;
+        if (gy == 0) e -= uc.z;
+        if (gy == ny - 1) e += uc.z;
+        if (z == 0) e -= uc.w;
+        if (z == nz - 1) e += uc.w;
         if (e != 0.f) tl.escaped.add(lam * e);
       }
-      clamp_state(Nn, Xn, Yn, Zn, tl.clipped);
-      // point sources of this plane (host-merged: at most one entry per cell)
-      while (sp < se) {
-        const TileSrc s = A.tsrc[sp];
-        if (s.z != z) break;
-        if (s.cell == tid) Nn += s.dN;
-        ++sp;
+      clamp_state(u.x, u.y, u.z, u.w, tl.clipped);
+      while (src.z == z) {
+        if (src.cell == tid) u.x += src.dN;
+        src.z = nz;
+        if (++sp < se) src = A.tsrc[sp];
       }
-      const float N0 = Nn;
-      const ChemOut co = chem_cell(P, cn, Nn, Xn, Yn, Zn, cy, cT);
-      tl.absorbed.add(N0 - Nn);
-      tl.sub += co.nsub;
-      tl.mx = max(tl.mx, (unsigned)co.nsub);
-      tl.err += co.err;
-      if (!isfinite(Nn) || !isfinite(cT) || !isfinite(Xn + Yn + Zn)) tl.nan += 1;
-      const long long o = (long long)z * plane + ocol;
-      A.out.N[o] = Nn; A.out.Fx[o] = Xn * cl; A.out.Fy[o] = Yn * cl; A.out.Fz[o] = Zn * cl;
-      A.y[o] = cy; A.T[o] = cT;
+      chem_tally_store(P, tl, cn, u, cy, cT, A.out, A.y, A.T, o);
     }
-    // rotate the register window
-#pragma unroll
-    for (int q = 0; q < 4; ++q) { um[q] = uc[q]; pm[q] = pc[q]; uc[q] = up[q]; pc[q] = pp[q]; }
+    um = uc; pm = pc; uc = up; pc = pp;
     cy = ny_; cT = nT_; cn = nn_;
+    rcur = rnx;
+    // z+3 (boundary-mapped) for the next plane's prefetch
+    if (++zz2 >= nz) { zz2 = PER ? zz2 - nz : nz - 1; }
+    p2 = (long long)zz2 * plane;
   }
   flush_tally<TY>(tl, A.slots, tile);
 }
@@ -202,7 +142,7 @@ int fused_tiles(int nx, int ny, int nz, int ty, int tz) {
 
 template <int TY>
 static constexpr size_t fused_smem() {
-  return sizeof(float) * 3 * 10 * (kTileX + 2) * (TY + 2);
+  return (size_t)3 * kRingRX * (TY + 2) * (sizeof(float4) * 2 + sizeof(float2));
 }
 
 template <int TY, bool PER>
@@ -535,7 +475,7 @@ __global__ void k_validate(const float* N, const float* y, const float* T, const
        i += (long long)gridDim.x * blockDim.x) {
     const float a = N[i], yy = y[i], t = T[i], h = nH[i];
     const bool ok = isfinite(a) && a >= 0.f && isfinite(yy) && yy >= 0.f && yy <= 1.f &&
-                    isfinite(t) && t > 0.f && isfinite(h) && h > 0.f;
+                    isfinite(t) && t > 0.f && isfinite(h) && h >= 1.17549435e-38f;
     b += ok ? 0u : 1u;
   }
   if (b) atomicAdd(bad, b);

@@ -2,15 +2,16 @@
 //
 // Same step as k_fused (Lax-Friedrichs M1 transport, section 2.2 and Appendix Eqs. A2/A5;
 // sources, section 2.3; chemistry operator Phi, Appendix Eq. A4), with the plane loads moved
-// off the compute threads. One producer warp streams each z-plane of the CTA's 32 x TY column
-// tile into a four-deep shared-memory ring with cp.async.bulk.tensor: a (32+8) x (TY+2) box of
-// each of N, Fx, Fy, Fz (one-cell halo; the x origin is 4 cells left so it stays 16-byte
-// aligned) and a 32 x TY box of y, T, nH. mbarriers signal full and empty stages. The TY
-// consumer warps turn each landed plane into a three-plane ring of vector records per slot,
-// (N, F/c), (Dxx, Dxy, Dxz, Dyy) N and (Dyz, Dzz) N, patching the slots that lie outside the
-// grid from global memory (boundary map; edge tiles only) and computing N D once per slot;
-// a neighbour then costs two or three vector loads. The cell update is the same as in
-// k_fused. Several planes are in flight per CTA without holding them in registers.
+// to the TMA engine. Thread 0 streams each z-plane of the CTA's 32 x TY column tile into a
+// three-deep shared-memory stage ring with cp.async.bulk.tensor: a (32+8) x (TY+2) box of each
+// of N, Fx, Fy, Fz (one-cell halo; the x origin is 4 cells left so it stays 16-byte aligned)
+// and a 32 x TY box of y, T, nH; one mbarrier per stage signals the landed bytes. A stage is
+// refilled right after the CTA barrier that ends its last use, so no thread waits on a free
+// stage and no warp is spent on producing. Every thread turns each landed plane into a
+// three-plane ring of vector records per slot, (N, F/c), (Dxx, Dxy, Dxz, Dyy) N and
+// (Dyz, Dzz) N, patching the slots that lie outside the grid from global memory (boundary
+// map; edge tiles only) and computing N D once per slot; a neighbour then costs two or three
+// vector loads. The cell update is the same as in k_fused.
 //
 // Used when nx is a multiple of 4 (the tensor-map row pitch must be a multiple of 16 bytes);
 // otherwise the step falls back to k_fused.
@@ -25,9 +26,11 @@ namespace aton {
 
 namespace {
 
-constexpr int kStages = 4;
+constexpr int kStages = 3;   // a stage is refilled two planes ahead of its use
 constexpr int kBoxX = kTileX + 8;          // x0-4 .. x0+35
-constexpr unsigned kWaitLimit = 1u << 26;  // polls before a wait is declared failed
+constexpr unsigned kWaitLimit = 1u << 26;            // polls before a wait is declared failed
+constexpr unsigned long long kWaitNs = 2000000000ull;  // or nanoseconds (2 s), whichever first
+constexpr unsigned kSuspendNs = 4000;                  // suspend-time hint of one poll
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -43,23 +46,30 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned
                : "memory");
 }
 
-__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
 
-// Bounded wait on the phase with the given parity. Returns false (and the caller raises the
-// error word) if the phase did not complete within kWaitLimit polls.
+// Bounded wait on the phase with the given parity. Each poll may suspend the thread until the
+// phase completes or kSuspendNs pass (so a waiting warp does not spin on the issue slots).
+// Returns false (and the caller raises the error word) if the phase did not complete within
+// kWaitLimit polls or kWaitNs nanoseconds.
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
   const unsigned a = smem_u32(bar);
+  unsigned long long t0 = 0;
   for (unsigned i = 0; i < kWaitLimit; ++i) {
     unsigned done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(a), "r"(parity)
+        : "r"(a), "r"(parity), "r"(kSuspendNs)
         : "memory");
     if (done) return true;
+    if (i == 0) t0 = global_ns();
+    else if (global_ns() - t0 > kWaitNs) return false;
   }
   return false;
 }
@@ -71,10 +81,6 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
       : "memory");
-}
-
-__device__ __forceinline__ void consumer_bar(int nthreads) {
-  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
 template <int TY>
@@ -89,25 +95,26 @@ struct Layout {
   static constexpr unsigned C_BYTES = 3u * CH * 4u;       // bytes landed per plane (chem)
   static constexpr size_t STAGE_BYTES = (size_t)kStages * STAGE * 4;
   static constexpr size_t RING_BYTES = (size_t)3 * PLR * (16 + 16 + 8);
-  static constexpr size_t BYTES = STAGE_BYTES + RING_BYTES + 2 * kStages * 8 + 128;
+  static constexpr size_t BYTES = STAGE_BYTES + RING_BYTES + kStages * 8 + 128;
 };
 
 }  // namespace
 
 template <int TY, bool PER>
-__global__ void __launch_bounds__(kTileX * (TY + 1)) k_fused_tma(const FusedArgs A,
-                                                                 const __grid_constant__ TmaMaps M) {
+__global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
+                                                           const __grid_constant__ TmaMaps M) {
   using L = Layout<TY>;
-  constexpr int TX = kTileX, NH = 2 * TX + 2 * TY, NC = TX * TY;
+  constexpr int TX = kTileX, NH = 2 * TX + 2 * TY;
   extern __shared__ __align__(128) float sm_raw[];
-  float* sm = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(sm_raw) + 127) & ~uintptr_t(127));
+  // 128-byte aligned base for the TMA boxes, as an offset from the shared array (so every
+  // access below stays a shared-memory access)
+  float* sm = sm_raw + ((128u - (smem_u32(sm_raw) & 127u)) & 127u) / 4;
   float* stage0 = sm;
   // ring of prepared planes: (N, Fx/c, Fy/c, Fz/c), (Dxx, Dxy, Dxz, Dyy) N, (Dyz, Dzz) N
   float4* RU = reinterpret_cast<float4*>(sm + kStages * L::STAGE);
   float4* RA = RU + 3 * L::PLR;
   float2* RB = reinterpret_cast<float2*>(RA + 3 * L::PLR);
   unsigned long long* full = reinterpret_cast<unsigned long long*>(RB + 3 * L::PLR);
-  unsigned long long* empty = full + kStages;
 
   const StepParams& P = A.P;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
@@ -118,190 +125,155 @@ __global__ void __launch_bounds__(kTileX * (TY + 1)) k_fused_tma(const FusedArgs
   const long long plane = (long long)nx * ny;
   const int tile = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   bool failed = false;
+  auto plane_of = [&](int z) {   // z in [-1, nz]
+    return z < 0 ? (PER ? nz - 1 : 0) : (z >= nz ? (PER ? 0 : nz - 1) : z);
+  };
+  // plane index k (plane z0 - 1 + k) into stage k % kStages; issued by thread 0 only
+  auto issue = [&](int k) {
+    const int s = k % kStages;
+    const int p = plane_of(z0 - 1 + k);
+    const bool chem = k >= 1 && k <= z1 - z0;
+    mbar_expect_tx(&full[s], L::U_BYTES + (chem ? L::C_BYTES : 0u));
+    float* st = stage0 + s * L::STAGE;
+    for (int q = 0; q < 4; ++q)
+      tma_load_3d(st + q * L::PLP, &M.u[A.in_buf][q], x0 - 4, y0 - 1, p, &full[s]);
+    if (chem)
+      for (int q = 0; q < 3; ++q)
+        tma_load_3d(st + 4 * L::PLP + q * L::CH, &M.chem[q], x0, y0, p, &full[s]);
+  };
+  auto wait = [&](int k) {   // plane k landed (skipped once a wait has failed)
+    if (!failed && !mbar_wait(&full[k % kStages], (k / kStages) & 1)) failed = true;
+  };
 
+  int issued = 0;   // planes issued so far (thread 0)
   if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], TY);
-    }
+    for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (; issued < kStages && issued < nplanes; ++issued) issue(issued);
   }
   __syncthreads();
 
   Tally tl;
-  if (ty == TY) {
-    // ---------------- producer warp: one lane issues the plane loads ----------------
-    if (tx == 0) {
-      for (int k = 0; k < nplanes; ++k) {
-        const int s = k % kStages;
-        if (k >= kStages && !mbar_wait(&empty[s], ((k / kStages) - 1) & 1)) failed = true;
-        int p = z0 - 1 + k;   // in [-1, nz]
-        if (p < 0) p = PER ? nz - 1 : 0;
-        if (p >= nz) p = PER ? 0 : nz - 1;
-        const bool chem = k >= 1 && k <= z1 - z0;
-        mbar_expect_tx(&full[s], L::U_BYTES + (chem ? L::C_BYTES : 0u));
-        float* st = stage0 + s * L::STAGE;
-        for (int q = 0; q < 4; ++q)
-          tma_load_3d(st + q * L::PLP, &M.u[A.in_buf][q], x0 - 4, y0 - 1, p, &full[s]);
-        if (chem)
-          for (int q = 0; q < 3; ++q)
-            tma_load_3d(st + 4 * L::PLP + q * L::CH, &M.chem[q], x0, y0, p, &full[s]);
-      }
-    }
-    __syncwarp();
-  } else {
-    // ---------------- consumer warps ----------------
-    const int gx = x0 + tx, gy = y0 + ty;
-    const bool act = gx < nx && gy < ny;
-    const int oslot = (ty + 1) * kBoxX + (tx + 4);       // stage slot
-    const int orslot = (ty + 1) * L::RX + (tx + 1);      // ring slot
-    // halo slot of this thread (if any) in tile coordinates
-    int hx = 0, hy = 0, hslot = -1, hrslot = -1;
-    if (tid < NH) {
-      if (tid < TX) { hx = tid; hy = -1; }
-      else if (tid < 2 * TX) { hx = tid - TX; hy = TY; }
-      else if (tid < 2 * TX + TY) { hx = -1; hy = tid - 2 * TX; }
-      else { hx = TX; hy = tid - 2 * TX - TY; }
-      hslot = (hy + 1) * kBoxX + (hx + 4);
-      hrslot = (hy + 1) * L::RX + (hx + 1);
-    }
-    const bool own_out = !act;
-    const bool halo_out = hslot >= 0 && (x0 + hx < 0 || x0 + hx >= nx || y0 + hy < 0 || y0 + hy >= ny);
-    const long long ocol = bc_map(gx, nx, PER) + (long long)nx * bc_map(gy, ny, PER);
-    const long long hcol = hslot >= 0 ? bc_map(x0 + hx, nx, PER) + (long long)nx * bc_map(y0 + hy, ny, PER) : 0;
-    const float rc = P.rc, cl = P.c, lam = P.lam;
-    const float hl = 0.5f * lam, cu = 1.f - 3.f * lam;
-    const float* __restrict__ gN = A.in.N;
-    const float* __restrict__ gX = A.in.Fx;
-    const float* __restrict__ gY = A.in.Fy;
-    const float* __restrict__ gZ = A.in.Fz;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const bool act = gx < nx && gy < ny;
+  const int oslot = (ty + 1) * kBoxX + (tx + 4);       // stage slot
+  const int orslot = (ty + 1) * L::RX + (tx + 1);      // ring slot
+  // halo slot of this thread (if any) in tile coordinates
+  int hx = 0, hy = 0, hslot = -1, hrslot = -1;
+  if (tid < NH) {
+    if (tid < TX) { hx = tid; hy = -1; }
+    else if (tid < 2 * TX) { hx = tid - TX; hy = TY; }
+    else if (tid < 2 * TX + TY) { hx = -1; hy = tid - 2 * TX; }
+    else { hx = TX; hy = tid - 2 * TX - TY; }
+    hslot = (hy + 1) * kBoxX + (hx + 4);
+    hrslot = (hy + 1) * L::RX + (hx + 1);
+  }
+  const bool own_out = !act;
+  const bool halo_out = hslot >= 0 && (x0 + hx < 0 || x0 + hx >= nx || y0 + hy < 0 || y0 + hy >= ny);
+  const long long ocol = bc_map(gx, nx, PER) + (long long)nx * bc_map(gy, ny, PER);
+  const long long hcol = hslot >= 0 ? bc_map(x0 + hx, nx, PER) + (long long)nx * bc_map(y0 + hy, ny, PER) : 0;
+  const float rc = P.rc, lam = P.lam;
+  const float hl = 0.5f * lam, cu = 1.f - 3.f * lam;
+  const float* __restrict__ gN = A.in.N;
+  const float* __restrict__ gX = A.in.Fx;
+  const float* __restrict__ gY = A.in.Fy;
+  const float* __restrict__ gZ = A.in.Fz;
 
-    // (N, F/c) of a slot of stage `st`: patched from global memory (boundary map) when the slot
-    // lies outside the grid, read from the TMA box otherwise.
-    auto prep = [&](const float* st, int slot, bool out, long long col, int p) {
-      float4 u;
-      if (out) {
-        const long long o = (long long)p * plane + col;
-        u = make_float4(__ldg(gN + o), __ldg(gX + o) * rc, __ldg(gY + o) * rc, __ldg(gZ + o) * rc);
-      } else {
-        u = make_float4(st[slot], st[L::PLP + slot] * rc, st[2 * L::PLP + slot] * rc,
-                        st[3 * L::PLP + slot] * rc);
-      }
-      return u;
-    };
-    // the prepared slot into ring plane r; returns the z flux (Fz/c, Dxz, Dyz, Dzz) N
-    auto put = [&](int r, int rslot, const float4& u) {
-      const ND6 d = m1_pressure(u.x, u.y, u.z, u.w);
-      RU[r * L::PLR + rslot] = u;
-      RA[r * L::PLR + rslot] = make_float4(d.xx, d.xy, d.xz, d.yy);
-      RB[r * L::PLR + rslot] = make_float2(d.yz, d.zz);
-      return make_float4(u.w, d.xz, d.yz, d.zz);
-    };
-    auto release = [&](int k) {
-      __syncwarp();
-      if (tx == 0) mbar_arrive(&empty[k % kStages]);
-    };
-    auto plane_of = [&](int z) {   // z in [-1, nz]
-      return z < 0 ? (PER ? nz - 1 : 0) : (z >= nz ? (PER ? 0 : nz - 1) : z);
-    };
+  // (N, F/c) of a slot of stage `st`: patched from global memory (boundary map) when the slot
+  // lies outside the grid, read from the TMA box otherwise.
+  auto prep = [&](const float* st, int slot, bool out, long long col, int p) {
+    float4 u;
+    if (out) {
+      const long long o = (long long)p * plane + col;
+      u = make_float4(__ldg(gN + o), __ldg(gX + o) * rc, __ldg(gY + o) * rc, __ldg(gZ + o) * rc);
+    } else {
+      u = make_float4(st[slot], st[L::PLP + slot] * rc, st[2 * L::PLP + slot] * rc,
+                      st[3 * L::PLP + slot] * rc);
+    }
+    return u;
+  };
+  // the prepared slot into ring plane r; returns the z flux (Fz/c, Dxz, Dyz, Dzz) N
+  auto put = [&](int r, int rslot, const float4& u) {
+    return ring_put(RU + r * L::PLR, RA + r * L::PLR, RB + r * L::PLR, rslot, u);
+  };
 
-    float4 um, pm, uc, pc;
-    // plane z0-1: the own column's state and z flux only
+  float4 um, pm, uc, pc;
+  // plane z0-1: the own column's state and z flux only
+  wait(0);
+  um = prep(stage0, oslot, own_out, ocol, plane_of(z0 - 1));
+  pm = z_flux(um);
+  // plane z0 into ring plane 1
+  {
+    wait(1);
+    const float* st = stage0 + (1 % kStages) * L::STAGE;
+    const int p = plane_of(z0);
+    uc = prep(st, oslot, own_out, ocol, p);
+    pc = put(1, orslot, uc);
+    if (hslot >= 0) put(1, hrslot, prep(st, hslot, halo_out, hcol, p));
+  }
+  int sp = A.tsrc_start[tile];
+  const int se = A.tsrc_start[tile + 1];
+  TileSrc src{nz, 0, 0.f, 0};
+  if (sp < se) src = A.tsrc[sp];
+  long long o = (long long)z0 * plane + ocol;
+  int rk = 1, rkn = 2;                  // ring planes of z and z+1 (plane index mod 3)
+  // stages of z and z+1 (plane index mod kStages) and the phase parity of the latter
+  int sk = 1 % kStages, skn = 2 % kStages;
+  unsigned pkn = (2 / kStages) & 1;
+
+  for (int z = z0; z < z1; ++z, o += plane) {
+    const int k = z - z0 + 1;           // plane index of z
+    float4 up, pp;
     {
-      if (!mbar_wait(&full[0], 0)) failed = true;
-      um = prep(stage0, oslot, own_out, ocol, plane_of(z0 - 1));
-      const ND6 d = m1_pressure(um.x, um.y, um.z, um.w);
-      pm = make_float4(um.w, d.xz, d.yz, d.zz);
-      release(0);
+      if (!failed && !mbar_wait(&full[skn], pkn)) failed = true;
+      const float* st = stage0 + skn * L::STAGE;
+      const int p = plane_of(z + 1);
+      up = prep(st, oslot, own_out, ocol, p);
+      pp = put(rkn, orslot, up);
+      if (hslot >= 0) put(rkn, hrslot, prep(st, hslot, halo_out, hcol, p));
     }
-    // plane z0 into ring plane 1
-    {
-      if (!mbar_wait(&full[1 % kStages], 0)) failed = true;
-      const float* st = stage0 + (1 % kStages) * L::STAGE;
-      const int p = plane_of(z0);
-      uc = prep(st, oslot, own_out, ocol, p);
-      pc = put(1, orslot, uc);
-      if (hslot >= 0) put(1, hrslot, prep(st, hslot, halo_out, hcol, p));
+    __syncthreads();
+    // every thread is done with plane k-1 (its box read for the ring, its chemistry fields
+    // read by the cell updates): its stage takes plane k-1+kStages
+    if (tid == 0 && !failed && k - 1 + kStages < nplanes) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(issued++);
     }
-    int sp = A.tsrc_start[tile];
-    const int se = A.tsrc_start[tile + 1];
-    long long o = (long long)z0 * plane + ocol;
-
-    for (int z = z0; z < z1; ++z, o += plane) {
-      const int k = z - z0 + 1;           // plane index of z
-      const int kn = k + 1;               // plane z+1
-      float4 up, pp;
-      {
-        if (!mbar_wait(&full[kn % kStages], (kn / kStages) & 1)) failed = true;
-        const float* st = stage0 + (kn % kStages) * L::STAGE;
-        const int p = plane_of(z + 1);
-        const int r = kn % 3;
-        up = prep(st, oslot, own_out, ocol, p);
-        pp = put(r, orslot, up);
-        if (hslot >= 0) put(r, hrslot, prep(st, hslot, halo_out, hcol, p));
+    if (act) {
+      const int c0 = rk * L::PLR + orslot;
+      float4 u = lf_update(RU + c0, RA + c0, RB + c0, uc, um, pm, up, pp, cu, hl);
+      if (!PER) {
+        float e = 0.f;
+        if (gx == 0) e -= uc.y;
+        if (gx == nx - 1) e += uc.y;
+        if (gy == 0) e -= uc.z;
+        if (gy == ny - 1) e += uc.z;
+        if (z == 0) e -= uc.w;
+        if (z == nz - 1) e += uc.w;
+        if (e != 0.f) tl.escaped.add(lam * e);
       }
-      consumer_bar(TX * TY);
-      if (act) {
-        const int r = k % 3;
-        const float4* U = RU + r * L::PLR + orslot;
-        const float4* Q = RA + r * L::PLR + orslot;
-        const float2* B = RB + r * L::PLR + orslot;
-        constexpr int RX = L::RX;
-        const float4 uL = U[-1], uR = U[1], uD = U[-RX], uU = U[RX];
-        const float4 aL = Q[-1], aR = Q[1], aD = Q[-RX], aU = Q[RX];
-        const float2 bD = B[-RX], bU = B[RX];
-        // sum over the six faces of (flux difference) - (neighbour sum); new u = (1-3 lam) u
-        // - lam/2 * that, the Lax-Friedrichs update written around the centre value.
-        // x faces carry (Fx, Dxx, Dxy, Dxz), y faces (Fy, Dxy, Dyy, Dyz), z (Fz, Dxz, Dyz, Dzz).
-        const float sN = (uR.y - uL.y) + (uU.z - uD.z) + (pp.x - pm.x) -
-                         ((uR.x + uL.x) + (uU.x + uD.x) + (up.x + um.x));
-        const float sX = (aR.x - aL.x) + (aU.y - aD.y) + (pp.y - pm.y) -
-                         ((uR.y + uL.y) + (uU.y + uD.y) + (up.y + um.y));
-        const float sY = (aR.y - aL.y) + (aU.w - aD.w) + (pp.z - pm.z) -
-                         ((uR.z + uL.z) + (uU.z + uD.z) + (up.z + um.z));
-        const float sZ = (aR.z - aL.z) + (bU.x - bD.x) + (pp.w - pm.w) -
-                         ((uR.w + uL.w) + (uU.w + uD.w) + (up.w + um.w));
-        float Nn = cu * uc.x - hl * sN;
-        float Xn = cu * uc.y - hl * sX;
-        float Yn = cu * uc.z - hl * sY;
-        float Zn = cu * uc.w - hl * sZ;
-        if (!PER) {
-          float e = 0.f;
-          if (gx == 0) e -= uc.y;
-          if (gx == nx - 1) e += uc.y;
-          if (gy == 0) e -= uc.z;
-          if (gy == ny - 1) e += uc.z;
-          if (z == 0) e -= uc.w;
-          if (z == nz - 1) e += uc.w;
-          if (e != 0.f) tl.escaped.add(lam * e);
-        }
-        clamp_state(Nn, Xn, Yn, Zn, tl.clipped);
-        while (sp < se) {
-          const TileSrc s = A.tsrc[sp];
-          if (s.z != z) break;
-          if (s.cell == tid) Nn += s.dN;
-          ++sp;
-        }
-        const float* C = stage0 + (k % kStages) * L::STAGE + 4 * L::PLP + tid;
-        float cy = C[0], cT = C[L::CH];
-        const float cn = C[2 * L::CH];
-        const float N0 = Nn;
-        const ChemOut co = chem_cell(P, cn, Nn, Xn, Yn, Zn, cy, cT);
-        tl.absorbed.add(N0 - Nn);
-        tl.sub += co.nsub;
-        tl.mx = max(tl.mx, (unsigned)co.nsub);
-        tl.err += co.err;
-        if (!isfinite(Nn) || !isfinite(cT) || !isfinite(Xn + Yn + Zn)) tl.nan += 1;
-        A.out.N[o] = Nn; A.out.Fx[o] = Xn * cl; A.out.Fy[o] = Yn * cl; A.out.Fz[o] = Zn * cl;
-        A.y[o] = cy; A.T[o] = cT;
+      clamp_state(u.x, u.y, u.z, u.w, tl.clipped);
+      while (src.z == z) {
+        if (src.cell == tid) u.x += src.dN;
+        src.z = nz;
+        if (++sp < se) src = A.tsrc[sp];
       }
-      release(k);
-      um = uc; pm = pc; uc = up; pc = pp;
+      const float* C = stage0 + sk * L::STAGE + 4 * L::PLP + tid;
+      chem_tally_store(P, tl, C[2 * L::CH], u, C[0], C[L::CH], A.out, A.y, A.T, o);
     }
-    (void)NC;
+    um = uc; pm = pc; uc = up; pc = pp;
+    rk = rkn;
+    rkn = rkn == 2 ? 0 : rkn + 1;
+    sk = skn;
+    if (++skn == kStages) { skn = 0; pkn ^= 1u; }
   }
   if (failed) atomicAdd(A.slots.timeout, 1u);
-  flush_tally<TY + 1>(tl, A.slots, tile);
+  // if a wait gave up, thread 0 waits (bounded) for the planes it issued last before the CTA
+  // exits, so no copy writes into shared memory afterwards
+  if (__syncthreads_or(failed) && tid == 0)
+    for (int k = max(0, issued - kStages); k < issued; ++k)
+      mbar_wait(&full[k % kStages], (k / kStages) & 1);
+  flush_tally<TY>(tl, A.slots, tile);
 }
 
 namespace {
@@ -315,7 +287,7 @@ cudaError_t set_tma_attr() {
 template <int TY, bool PER>
 cudaError_t launch_tma_t(const FusedArgs& a, const TmaMaps& m, cudaStream_t s) {
   dim3 grid((a.P.nx + kTileX - 1) / kTileX, (a.P.ny + TY - 1) / TY, (a.P.nz + a.tz - 1) / a.tz);
-  dim3 block(kTileX, TY + 1);
+  dim3 block(kTileX, TY);
   k_fused_tma<TY, PER><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);
   return cudaGetLastError();
 }

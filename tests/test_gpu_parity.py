@@ -302,3 +302,25 @@ def test_autotune_leaves_the_state_untouched(small):
     a.step(2)
     assert a.synchronize() == 0
     a.close()
+
+
+# clumping factors C_R = max(1, 1e3 nH^0.7), C_I = max(1, 10 nH^0.2): 2.6 and 1.8 at the mean
+# density of the lognormal box, up to ~40 and ~3 in its densest cells
+CLUMP = dict(clump_R_A=1e3, clump_R_b=0.7, clump_I_A=10.0, clump_I_b=0.2)
+
+
+@pytest.mark.parametrize("mode", [A.MODE_FUSED, A.MODE_UNFUSED])
+def test_clumping_chemistry_matches_the_oracle(small, small_oracle, mode):
+    """Section 3.2.1, Eq. 15 (read with the signs of Eq. 14): the clumping factors multiply the
+    recombination and photo-ionisation terms; parity with the oracle under the same gates."""
+    st, idx, rate, run = small
+    orc, ob, _ = run_oracle(st, idx, rate, run, 100, **CLUMP)
+    f, b, d, rc = run_gpu(st, idx, rate, run, 100, mode=mode, **CLUMP)
+    assert rc == 0
+    e = errors(f, orc)
+    print("clumping errors", mode, e)
+    assert_gates(e, f"clumping mode {mode}")
+    assert abs(budget_closure(b)) <= 1e-6
+    assert b["absorbed"] == pytest.approx(ob["absorbed"], rel=1e-3)
+    # the factors change the answer far beyond the gates
+    assert np.abs(orc["x"] - small_oracle[0]["x"]).max() > 1e-2
