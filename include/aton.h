@@ -269,6 +269,71 @@ int aton_mlp_train_step(aton_mlp_handle m, const float* X, const float* T, int n
                         double* loss);
 int aton_mlp_synchronize(aton_mlp_handle m);
 
+/* ---------------------------------------------------------------------------------------
+ * Ionisation and radiation statistics of the current state (section 4: the volume-weighted
+ * ionised fraction x_v and the distribution of the neutral fraction; the mean intensity J21
+ * and the photo-ionisation rate Gamma12 and their distribution; the density dependence
+ * (1-x)(nH) and J21(nH) with the mean per density bin, compared with photo-ionisation
+ * equilibrium under a uniform or self-shielded field).
+ *
+ * Readings: Gamma = c sigma_n N (no sub-grid clumping factor), Gamma12 = Gamma / 1e-12 s^-1.
+ * J21 is the Lyman-limit mean intensity, in 1e-21 erg s^-1 cm^-2 Hz^-1 sr^-1, of a spectrum
+ * J_nu = J_0 (nu/nu_0)^-alpha with the same photo-ionisation rate when sigma falls as nu^-3:
+ * Gamma = 4 pi J_0 sigma_0 / (h (alpha + 3)), sigma_0 = 6.30e-18 cm^2.
+ * Histograms use log-spaced bins: edge k of a quantity with range [lo, hi] and nb bins is
+ * 10^(log10 lo + k (log10 hi - log10 lo) / nb) rounded to float; a value v lies in bin b when
+ * edge[b] <= v < edge[b+1], values below edge[1] count in bin 0 and values at or above
+ * edge[nb-1] in bin nb-1. The decision compares the stored float values with the float edges
+ * (J21 bins compare N with the edges divided by the J21-per-N factor), so it is exact.
+ * --------------------------------------------------------------------------------------- */
+#define ATON_STATS_MAX_BINS 64
+
+typedef struct {
+  int nb_nH, nb_y, nb_J;      /* bins of nH, of the neutral fraction y = 1-x, of J21 (1..64) */
+  double nH_lo, nH_hi;        /* [cm^-3] range of the density bins */
+  double y_lo, y_hi;          /* range of the neutral-fraction bins */
+  double J21_lo, J21_hi;      /* range of the J21 bins */
+  double spectral_index;      /* alpha of the J21 reading (default 1) */
+  double nH_plateau;          /* J21 plateau J0: mean over cells with nH below this (1e-3) */
+} aton_stats_params;
+
+typedef struct {
+  double x_volume, x_mass;        /* volume-weighted and mass-weighted ionised fraction */
+  double gamma12_volume;          /* volume-averaged Gamma12 */
+  double J21_volume, J21_plateau; /* volume-averaged J21; its mean over nH < nH_plateau */
+  double T_volume, T_mass;        /* volume- and mass-weighted temperature [K] */
+  double photons;                 /* sum N V */
+  int64_t cells, plateau_cells;
+} aton_stats;
+
+/* Defaults: 48 density bins over [1e-6, 1] cm^-3, 48 neutral-fraction bins over [1e-7, 1],
+ * 48 J21 bins over [1e-6, 1e4], alpha = 1, plateau below 1e-3 cm^-3. */
+int aton_default_stats_params(aton_stats_params* p);
+
+/* Statistics of the state after the steps queued so far (waits for them). Host output arrays,
+ * each may be NULL: hist_y [nb_nH][nb_y] and hist_J [nb_nH][nb_J] cell counts (row-major,
+ * density bin first), bin_count [nb_nH] cells per density bin, bin_mean_y and bin_mean_J21
+ * [nb_nH] volume averages of y and J21 per density bin (0 where the bin is empty).
+ * One pass over N, y, T, nH (16 bytes per cell) in device kernels; counts and histograms are
+ * exact, sums are per-thread compensated FP32 reduced in FP64 in a fixed order (deterministic).
+ * Errors: BADARG (NULL handle, params or stats; bins outside 1..64; a range with lo <= 0 or
+ * hi <= lo), STATE (no fields), NOMEM, CUDA. */
+int aton_ionisation_stats(aton_handle h, const aton_stats_params* p, aton_stats* s,
+                          uint64_t* hist_y, uint64_t* hist_J, uint64_t* bin_count,
+                          double* bin_mean_y, double* bin_mean_J21);
+
+/* Neutral fraction in photo-ionisation equilibrium, (1-x) Gamma(nH) = alpha_B(T) nH x^2
+ * (section 3.2.1, Eq. 14 at steady state, no collisional ionisation), for the field models of
+ * section 4: Gamma(nH) = Gamma_0 exp(-(nH/n_star)^power), power 0 (uniform J0), 1 (J1) or 4
+ * (J4; read as exp(-(nH/n*)^4), the form of the figure caption), with Gamma_0 the rate of
+ * J21_0 under the reading above and alpha_B the Hui & Gnedin (1997) case-B fit. Written without
+ * cancellation: x = 2G / (G + sqrt(G^2 + 4 a G)), y = a x^2 / G with G = Gamma, a = alpha nH.
+ * Host computation (a closed form per density value). Errors: BADARG (NULL arrays, n < 0,
+ * J21_0 < 0, T <= 0, n_star <= 0 with power > 0, power not 0, 1 or 4, alpha <= -3). */
+int aton_equilibrium_neutral_fraction(const double* nH, int n, double J21_0, double n_star,
+                                      int power, double T, double spectral_index,
+                                      double* y_out);
+
 /* Static description of a status code. */
 const char* aton_strerror(int code);
 

@@ -33,8 +33,10 @@ EXPORTS = (
     "aton_mlp_create", "aton_mlp_destroy", "aton_mlp_num_params", "aton_mlp_set_params",
     "aton_mlp_get_params", "aton_mlp_fit_norm", "aton_mlp_get_norm", "aton_mlp_set_norm",
     "aton_mlp_features", "aton_mlp_forward", "aton_mlp_loss_grad", "aton_mlp_train_step",
-    "aton_mlp_synchronize",
+    "aton_mlp_synchronize", "aton_default_stats_params", "aton_ionisation_stats",
+    "aton_equilibrium_neutral_fraction",
 )
+STATS_MAX_BINS = 64
 
 
 class aton_params(C.Structure):
@@ -56,6 +58,20 @@ class aton_diag(C.Structure):
 
 class aton_surrogate_params(C.Structure):
     _fields_ = [("enabled", C.c_int), ("gate_substeps", C.c_double), ("residual_max", C.c_double)]
+
+
+class aton_stats_params(C.Structure):
+    _fields_ = [("nb_nH", C.c_int), ("nb_y", C.c_int), ("nb_J", C.c_int),
+                ("nH_lo", C.c_double), ("nH_hi", C.c_double), ("y_lo", C.c_double),
+                ("y_hi", C.c_double), ("J21_lo", C.c_double), ("J21_hi", C.c_double),
+                ("spectral_index", C.c_double), ("nH_plateau", C.c_double)]
+
+
+class aton_stats(C.Structure):
+    _fields_ = [("x_volume", C.c_double), ("x_mass", C.c_double),
+                ("gamma12_volume", C.c_double), ("J21_volume", C.c_double),
+                ("J21_plateau", C.c_double), ("T_volume", C.c_double), ("T_mass", C.c_double),
+                ("photons", C.c_double), ("cells", C.c_int64), ("plateau_cells", C.c_int64)]
 
 
 class AtonError(RuntimeError):
@@ -124,6 +140,11 @@ def load():
     L.aton_mlp_loss_grad.argtypes = [_VP, _VP, _VP, C.c_int, _VP, C.POINTER(C.c_double)]
     L.aton_mlp_train_step.argtypes = [_VP, _VP, _VP, C.c_int, C.c_float, C.POINTER(C.c_double)]
     L.aton_mlp_synchronize.argtypes = [_VP]
+    L.aton_default_stats_params.argtypes = [C.POINTER(aton_stats_params)]
+    L.aton_ionisation_stats.argtypes = [_VP, C.POINTER(aton_stats_params), C.POINTER(aton_stats),
+                                        _VP, _VP, _VP, _VP, _VP]
+    L.aton_equilibrium_neutral_fraction.argtypes = [_VP, C.c_int, C.c_double, C.c_double,
+                                                    C.c_int, C.c_double, C.c_double, _VP]
     L.aton_last_message.argtypes = []
     L.aton_last_message.restype = C.c_char_p
     for name in EXPORTS:
@@ -292,6 +313,25 @@ class Aton:
         _check(self.L.aton_get_diag(self.h, C.byref(d)), "aton_get_diag")
         return {k: getattr(d, k) for k, _ in aton_diag._fields_}
 
+    def ionisation_stats(self, **params):
+        """aton_ionisation_stats with the defaults overridden by ``params`` (fields of
+        aton_stats_params). Returns the summary fields plus the arrays hist_y (nb_nH, nb_y),
+        hist_J (nb_nH, nb_J), bin_count, bin_mean_y, bin_mean_J21 (nb_nH) and the params."""
+        p = stats_params(**params)
+        s = aton_stats()
+        hy = np.zeros((p.nb_nH, p.nb_y), np.uint64)
+        hj = np.zeros((p.nb_nH, p.nb_J), np.uint64)
+        bc = np.zeros(p.nb_nH, np.uint64)
+        my = np.zeros(p.nb_nH, np.float64)
+        mj = np.zeros(p.nb_nH, np.float64)
+        _check(self.L.aton_ionisation_stats(self.h, C.byref(p), C.byref(s), hy.ctypes.data,
+                                            hj.ctypes.data, bc.ctypes.data, my.ctypes.data,
+                                            mj.ctypes.data), "aton_ionisation_stats")
+        out = {k: getattr(s, k) for k, _ in aton_stats._fields_}
+        out.update(hist_y=hy, hist_J=hj, bin_count=bc, bin_mean_y=my, bin_mean_J21=mj,
+                   params={k: getattr(p, k) for k, _ in aton_stats_params._fields_})
+        return out
+
     def last_error_cells(self):
         n = C.c_int64()
         _check(self.L.aton_last_error_cells(self.h, C.byref(n)), "aton_last_error_cells")
@@ -332,6 +372,28 @@ def photon_sum_static(N, cell_volume, stream=None):
     _check(load().aton_photon_sum_static(ptr, int(N.numel()), float(cell_volume), C.byref(out), s),
            "aton_photon_sum_static")
     return out.value
+
+
+def stats_params(**params):
+    """aton_stats_params: the library defaults with ``params`` overriding fields."""
+    p = aton_stats_params()
+    _check(load().aton_default_stats_params(C.byref(p)), "aton_default_stats_params")
+    for k, v in params.items():
+        if k not in dict(aton_stats_params._fields_):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def equilibrium_neutral_fraction(nH, J21_0, n_star=1.0, power=0, T=1e4, spectral_index=1.0):
+    """aton_equilibrium_neutral_fraction over the densities nH (any float array)."""
+    n = np.ascontiguousarray(nH, dtype=np.float64).ravel()
+    y = np.empty_like(n)
+    _check(load().aton_equilibrium_neutral_fraction(n.ctypes.data, int(n.size), float(J21_0),
+                                                    float(n_star), int(power), float(T),
+                                                    float(spectral_index), y.ctypes.data),
+           "aton_equilibrium_neutral_fraction")
+    return y.reshape(np.shape(nH))
 
 
 class Mlp:

@@ -14,8 +14,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libaton.so")
-SOURCES = ["aton_capi.cu", "aton_kernels.cu", "aton_tma.cu", "aton_mlp.cu", "aton_static.cu"]
-HEADERS = ["aton_device.cuh", "aton_internal.h", "aton_step_common.cuh", "aton_mlp.cuh"]
+SOURCES = ["aton_capi.cu", "aton_kernels.cu", "aton_tma.cu", "aton_mlp.cu", "aton_static.cu",
+           "aton_stats.cu"]
+HEADERS = ["aton_device.cuh", "aton_internal.h", "aton_step_common.cuh", "aton_mlp.cuh",
+           "aton_stats.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # The kernels use the hardware approximations of division, reciprocal square root, square root,
 # exp2 and log2 (a few ulp) and flush FP32 denormals: every denominator in the kernels is

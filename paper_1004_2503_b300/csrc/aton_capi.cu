@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "aton_internal.h"
+#include "aton_stats.cuh"
 
 using namespace aton;
 
@@ -96,6 +97,11 @@ struct aton_ctx {
   aton_surrogate_params sur_p{};
   int* sur_list = nullptr;
   int* sur_count = nullptr;
+  // statistics pass
+  float* st_edges = nullptr;
+  double* st_part = nullptr;
+  double* st_out = nullptr;
+  unsigned long long* st_u64 = nullptr;
 
   cudaStream_t stream() const { return user ? user : own; }
 };
@@ -355,6 +361,157 @@ void aton_default_params(aton_params* p) {
   p->y_floor = 1e-6;
 }
 
+// ---------------------------------------------------------------------------------------
+// Ionisation and radiation statistics (section 4)
+// ---------------------------------------------------------------------------------------
+static constexpr double kHPlanck = 6.62607015e-27;  // erg s
+static constexpr double kSigma0 = 6.30e-18;         // HI cross-section at the Lyman limit, cm^2
+static constexpr double kPi = 3.14159265358979323846;
+
+// Gamma per unit J21 under the power-law reading: Gamma = 4 pi J_0 sigma_0 / (h (alpha + 3))
+static double gamma_per_J21(double alpha) {
+  return 4.0 * kPi * kSigma0 * 1e-21 / (kHPlanck * (alpha + 3.0));
+}
+
+int aton_default_stats_params(aton_stats_params* p) {
+  if (!p) return fail(ATON_ERR_BADARG, "p is NULL");
+  p->nb_nH = 48; p->nb_y = 48; p->nb_J = 48;
+  p->nH_lo = 1e-6; p->nH_hi = 1.0;
+  p->y_lo = 1e-7; p->y_hi = 1.0;
+  p->J21_lo = 1e-6; p->J21_hi = 1e4;
+  p->spectral_index = 1.0;
+  p->nH_plateau = 1e-3;
+  return ATON_OK;
+}
+
+// edge k of nb log-spaced bins over [lo, hi], divided by div, rounded to float
+static void log_edges(double lo, double hi, int nb, double div, float* E) {
+  const double a = std::log10(lo), b = std::log10(hi);
+  for (int k = 0; k <= nb; ++k) E[k] = (float)(std::pow(10.0, a + (b - a) * k / nb) / div);
+}
+
+static bool good_range(double lo, double hi) {
+  return std::isfinite(lo) && std::isfinite(hi) && lo > 0.0 && hi > lo;
+}
+
+int aton_ionisation_stats(aton_handle h, const aton_stats_params* p, aton_stats* s,
+                          uint64_t* hist_y, uint64_t* hist_J, uint64_t* bin_count,
+                          double* bin_mean_y, double* bin_mean_J21) {
+  if (int rc = check_h(h)) return rc;
+  if (!p || !s) return fail(ATON_ERR_BADARG, "params or stats is NULL");
+  if (!h->fields_set) return fail(ATON_ERR_STATE, "aton_set_fields has not been called");
+  const int MB = kStatsMaxBins;
+  if (p->nb_nH < 1 || p->nb_nH > MB || p->nb_y < 1 || p->nb_y > MB || p->nb_J < 1 || p->nb_J > MB)
+    return fail(ATON_ERR_BADARG, "bins must be 1..%d", MB);
+  if (!good_range(p->nH_lo, p->nH_hi) || !good_range(p->y_lo, p->y_hi) ||
+      !good_range(p->J21_lo, p->J21_hi))
+    return fail(ATON_ERR_BADARG, "a bin range has lo <= 0 or hi <= lo");
+  if (!(p->spectral_index > -3.0) || !std::isfinite(p->spectral_index))
+    return fail(ATON_ERR_BADARG, "spectral_index must be finite and > -3");
+  const size_t n_u64 = 2 * (size_t)MB * MB + MB + 1;
+  const size_t n_out = kStatsScalars + 2 * MB;
+  if (!h->st_edges) {
+    CU(cudaMalloc(&h->st_edges, sizeof(float) * 3 * (MB + 1)));
+    CU(cudaMalloc(&h->st_part, sizeof(double) * kStatsBlocks * (kStatsScalars + 2 * MB)));
+    CU(cudaMalloc(&h->st_out, sizeof(double) * n_out));
+    CU(cudaMalloc(&h->st_u64, sizeof(unsigned long long) * n_u64));
+  }
+  // J21 = kJ N: Gamma = c sigma_n N and Gamma per J21 from the reading
+  const double kJ = h->c * h->prm.sigma_n / gamma_per_J21(p->spectral_index);
+  std::vector<float> E(3 * (MB + 1), 0.f);
+  log_edges(p->nH_lo, p->nH_hi, p->nb_nH, 1.0, &E[0]);
+  log_edges(p->y_lo, p->y_hi, p->nb_y, 1.0, &E[MB + 1]);
+  log_edges(p->J21_lo, p->J21_hi, p->nb_J, kJ, &E[2 * (MB + 1)]);
+  cudaStream_t st = h->stream();
+  CU(cudaMemcpyAsync(h->st_edges, E.data(), sizeof(float) * E.size(), cudaMemcpyHostToDevice, st));
+  CU(cudaMemsetAsync(h->st_u64, 0, sizeof(unsigned long long) * n_u64, st));
+  StatsArgs a{};
+  a.N = h->f[h->cur][0];
+  a.y = h->y;
+  a.T = h->T;
+  a.nH = h->nH;
+  a.ncell = h->ncell;
+  a.nb_n = p->nb_nH; a.nb_y = p->nb_y; a.nb_J = p->nb_J;
+  a.edges = h->st_edges;
+  const double lo[3] = {p->nH_lo, p->y_lo, p->J21_lo / kJ};
+  const double hi[3] = {p->nH_hi, p->y_hi, p->J21_hi / kJ};
+  const int nb[3] = {p->nb_nH, p->nb_y, p->nb_J};
+  for (int q = 0; q < 3; ++q) {
+    a.g[2 * q] = (float)std::log2(lo[q]);
+    a.g[2 * q + 1] = (float)(nb[q] / std::log2(hi[q] / lo[q]));
+  }
+  a.n_plateau = (float)p->nH_plateau;
+  a.part_scalar = h->st_part;
+  a.part_bins = h->st_part + (size_t)kStatsBlocks * kStatsScalars;
+  a.hist_y = h->st_u64;
+  a.hist_J = h->st_u64 + (size_t)MB * MB;
+  a.bin_count = h->st_u64 + 2 * (size_t)MB * MB;
+  a.plateau_count = h->st_u64 + 2 * (size_t)MB * MB + MB;
+  CU(launch_stats(a, h->st_out, st));
+  std::vector<double> out(n_out);
+  std::vector<unsigned long long> u(n_u64);
+  CU(cudaMemcpyAsync(out.data(), h->st_out, sizeof(double) * n_out, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(u.data(), h->st_u64, sizeof(unsigned long long) * n_u64,
+                     cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  const double n = (double)h->ncell;
+  const double sy = out[0], sn = out[1], sny = out[2], sN = out[3], sT = out[4], snT = out[5],
+               sNp = out[6];
+  const unsigned long long cp = u[2 * (size_t)MB * MB + MB];
+  s->x_volume = 1.0 - sy / n;
+  s->x_mass = 1.0 - sny / sn;
+  s->gamma12_volume = h->c * h->prm.sigma_n * sN / n / 1e-12;
+  s->J21_volume = kJ * sN / n;
+  s->J21_plateau = cp ? kJ * sNp / (double)cp : 0.0;
+  s->T_volume = sT / n;
+  s->T_mass = snT / sn;
+  s->photons = sN * h->V;
+  s->cells = h->ncell;
+  s->plateau_cells = (int64_t)cp;
+  for (int b = 0; b < p->nb_nH; ++b) {
+    if (hist_y)
+      for (int k = 0; k < p->nb_y; ++k) hist_y[b * p->nb_y + k] = u[b * p->nb_y + k];
+    if (hist_J)
+      for (int k = 0; k < p->nb_J; ++k) hist_J[b * p->nb_J + k] = u[(size_t)MB * MB + b * p->nb_J + k];
+    const unsigned long long c = u[2 * (size_t)MB * MB + b];
+    if (bin_count) bin_count[b] = c;
+    const double* bs = out.data() + kStatsScalars + 2 * b;
+    if (bin_mean_y) bin_mean_y[b] = c ? bs[0] / (double)c : 0.0;
+    if (bin_mean_J21) bin_mean_J21[b] = c ? kJ * bs[1] / (double)c : 0.0;
+  }
+  return ATON_OK;
+}
+
+// case-B recombination rate, Hui & Gnedin (1997), FP64 (host)
+static double alpha_B_host(double T) {
+  const double lam = 2.0 * 157807.0 / T;
+  return 2.753e-14 * std::pow(lam, 1.5) / std::pow(1.0 + std::pow(lam / 2.740, 0.407), 2.242);
+}
+
+int aton_equilibrium_neutral_fraction(const double* nH, int n, double J21_0, double n_star,
+                                      int power, double T, double spectral_index,
+                                      double* y_out) {
+  if ((!nH || !y_out) && n > 0) return fail(ATON_ERR_BADARG, "NULL array");
+  if (n < 0) return fail(ATON_ERR_BADARG, "n < 0");
+  if (!(J21_0 >= 0.0) || !(T > 0.0)) return fail(ATON_ERR_BADARG, "J21_0 < 0 or T <= 0");
+  if (power != 0 && power != 1 && power != 4) return fail(ATON_ERR_BADARG, "power must be 0, 1 or 4");
+  if (power > 0 && !(n_star > 0.0)) return fail(ATON_ERR_BADARG, "n_star <= 0");
+  if (!(spectral_index > -3.0)) return fail(ATON_ERR_BADARG, "spectral_index <= -3");
+  const double G0 = J21_0 * gamma_per_J21(spectral_index);
+  const double al = alpha_B_host(T);
+  for (int i = 0; i < n; ++i) {
+    const double G = power == 0 ? G0 : G0 * std::exp(-std::pow(nH[i] / n_star, power));
+    const double a = al * nH[i];
+    if (!(G > 0.0)) {
+      y_out[i] = 1.0;
+      continue;
+    }
+    const double q = G + std::sqrt(G * G + 4.0 * a * G);
+    y_out[i] = 4.0 * a * G / (q * q);   // a x^2 / G with x = 2G / q
+  }
+  return ATON_OK;
+}
+
 const char* aton_strerror(int code) {
   switch (code) {
     case ATON_OK: return "ok";
@@ -382,6 +539,7 @@ void aton_finalize(aton_handle h) {
   free_slots(h->slots);
   cudaFree(h->d_src_idx); cudaFree(h->d_src_dN); cudaFree(h->d_tstart); cudaFree(h->d_tsrc);
   cudaFree(h->sur_list); cudaFree(h->sur_count);
+  cudaFree(h->st_edges); cudaFree(h->st_part); cudaFree(h->st_out); cudaFree(h->st_u64);
   if (h->own) cudaStreamDestroy(h->own);
   delete h;
 }
