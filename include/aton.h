@@ -334,6 +334,46 @@ int aton_equilibrium_neutral_fraction(const double* nH, int n, double J21_0, dou
                                       int power, double T, double spectral_index,
                                       double* y_out);
 
+/* ---------------------------------------------------------------------------------------
+ * Source model of the post-processing (section 2.3): star particles of snapshot p+1 emit over
+ * the interval [t_p, t_{p+1}] (length D) at a rate that spreads the photons they emit inside it
+ * over the whole interval. A star of lifetime L emits Q = photons_per_baryon * mass / m_H
+ * photons uniformly over its lifetime, Ndot = Q / L. With a = its age at t_{p+1} and
+ * a_p = a - D its age at t_p:
+ *   a_p >= L       no emission (cell -1, rate 0);
+ *   a_p < 0        born inside the interval, emits for min(a, L): rate = min(a, L)/D Ndot;
+ *   0 <= a_p < L   emits for min(D, L - a_p): rate = min(D, L - a_p)/D Ndot.
+ * Readings: the printed "(a_{p+1} - a*)" and "min(1, L - a_p)" mix an age with a time and a
+ * number with a time; the emitting time inside the interval is read instead, which keeps
+ * every star's photons exact. The effective rate is Ndot_eff = rate f_esc B(t) (Eq. 16) with
+ * the boost factor B(t) = max(1, a_b exp(k_b / t)) (Eq. 17 prints min, which would make the
+ * boost never exceed 1; its table's a_b and k_b only boost with max), t the age of the Universe.
+ * The cell is the nearest grid point, floor(x/dx) wrapped periodically.
+ * --------------------------------------------------------------------------------------- */
+typedef struct {
+  double x, y, z;             /* position [cm] */
+  double mass;                /* stellar mass [g] */
+  double age;                 /* age at the end of the interval, a_{p+1} [s] (>= 0) */
+  double lifetime;            /* ionising lifetime L [s] (> 0; drawn by the caller) */
+  double photons_per_baryon;  /* ionising photons per stellar baryon over the lifetime */
+} aton_star;
+
+typedef struct {
+  double interval;            /* D = t_{p+1} - t_p [s] (> 0) */
+  double f_esc;               /* escape fraction (>= 0) */
+  double boost_a, boost_k;    /* B = max(1, boost_a exp(boost_k / t)); boost_a <= 0: B = 1 */
+  double t_universe;          /* age of the Universe [s] at which B is evaluated (> 0) */
+} aton_source_model;
+
+/* Cell (-1 when the star is not active inside the interval: zero emitting time) and effective
+ * rate [photons/s] of each star, for a grid of nx*ny*nz cells of size dx. Host arrays; no
+ * handle needed. The output feeds aton_add_sources (cells >= 0), which merges stars that
+ * share a cell.
+ * Errors: BADARG (NULL arrays with n > 0, n < 0, bad grid or model, a star with negative or
+ * non-finite mass/age/photon yield, non-positive lifetime, non-finite position). */
+int aton_star_sources(const aton_star* stars, int64_t n, const aton_source_model* m, int nx,
+                      int ny, int nz, double dx, int64_t* cell, double* rate);
+
 /* Static description of a status code. */
 const char* aton_strerror(int code);
 

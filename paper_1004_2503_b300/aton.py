@@ -34,8 +34,11 @@ EXPORTS = (
     "aton_mlp_get_params", "aton_mlp_fit_norm", "aton_mlp_get_norm", "aton_mlp_set_norm",
     "aton_mlp_features", "aton_mlp_forward", "aton_mlp_loss_grad", "aton_mlp_train_step",
     "aton_mlp_synchronize", "aton_default_stats_params", "aton_ionisation_stats",
-    "aton_equilibrium_neutral_fraction",
+    "aton_equilibrium_neutral_fraction", "aton_star_sources",
 )
+# layout of aton_star: 7 doubles
+STAR_DTYPE = np.dtype([("x", "<f8"), ("y", "<f8"), ("z", "<f8"), ("mass", "<f8"), ("age", "<f8"),
+                       ("lifetime", "<f8"), ("photons_per_baryon", "<f8")])
 STATS_MAX_BINS = 64
 
 
@@ -72,6 +75,11 @@ class aton_stats(C.Structure):
                 ("gamma12_volume", C.c_double), ("J21_volume", C.c_double),
                 ("J21_plateau", C.c_double), ("T_volume", C.c_double), ("T_mass", C.c_double),
                 ("photons", C.c_double), ("cells", C.c_int64), ("plateau_cells", C.c_int64)]
+
+
+class aton_source_model(C.Structure):
+    _fields_ = [("interval", C.c_double), ("f_esc", C.c_double), ("boost_a", C.c_double),
+                ("boost_k", C.c_double), ("t_universe", C.c_double)]
 
 
 class AtonError(RuntimeError):
@@ -145,6 +153,8 @@ def load():
                                         _VP, _VP, _VP, _VP, _VP]
     L.aton_equilibrium_neutral_fraction.argtypes = [_VP, C.c_int, C.c_double, C.c_double,
                                                     C.c_int, C.c_double, C.c_double, _VP]
+    L.aton_star_sources.argtypes = [_VP, C.c_int64, C.POINTER(aton_source_model), C.c_int,
+                                    C.c_int, C.c_int, C.c_double, _VP, _VP]
     L.aton_last_message.argtypes = []
     L.aton_last_message.restype = C.c_char_p
     for name in EXPORTS:
@@ -394,6 +404,22 @@ def equilibrium_neutral_fraction(nH, J21_0, n_star=1.0, power=0, T=1e4, spectral
                                                     float(spectral_index), y.ctypes.data),
            "aton_equilibrium_neutral_fraction")
     return y.reshape(np.shape(nH))
+
+
+def star_sources(stars, shape, dx, interval, f_esc=1.0, boost_a=0.0, boost_k=0.0,
+                 t_universe=1.0):
+    """aton_star_sources: (cell, rate) of each star (a STAR_DTYPE array) on a grid of shape
+    (nz, ny, nx) and cell size dx; cell -1 marks stars that do not emit in the interval."""
+    st = np.ascontiguousarray(stars, dtype=STAR_DTYPE)
+    nz, ny, nx = shape
+    m = aton_source_model(float(interval), float(f_esc), float(boost_a), float(boost_k),
+                          float(t_universe))
+    cell = np.empty(st.size, np.int64)
+    rate = np.empty(st.size, np.float64)
+    _check(load().aton_star_sources(st.ctypes.data, int(st.size), C.byref(m), int(nx), int(ny),
+                                    int(nz), float(dx), cell.ctypes.data, rate.ctypes.data),
+           "aton_star_sources")
+    return cell, rate
 
 
 class Mlp:

@@ -147,3 +147,55 @@ def subsample_state(state, src_idx, src_rate, shape, origin=(0, 0, 0)):
     m = (k >= oz) & (k < oz + sz) & (j >= oy) & (j < oy + sy) & (i >= ox) & (i < ox + sx)
     loc = (i[m] - ox) + sx * ((j[m] - oy) + sy * (k[m] - oz))
     return st, loc.astype(np.int64), src_rate[m].copy()
+
+
+# ------------------------------------------------------------------------------------------
+# Snapshot sequences of star particles (section 2.3 post-processing; the cosmological runs'
+# star lists are not available). Stars form at the highest density peaks at uniformly random
+# times, more of them in every interval; each snapshot lists every star born before it with its
+# age then. Lifetimes are drawn uniformly in [5, 20] Myr and yields uniformly in [24 000,
+# 98 000] ionising photons per stellar baryon, the ranges section 2.3 quotes; the star mass is
+# the 12.5 Mpc/h run's minimum star particle mass of its parameter table.
+# ------------------------------------------------------------------------------------------
+MSUN = 1.98892e33             # g
+STAR_FIELDS = [("x", "<f8"), ("y", "<f8"), ("z", "<f8"), ("mass", "<f8"), ("age", "<f8"),
+               ("lifetime", "<f8"), ("photons_per_baryon", "<f8")]
+
+
+def star_snapshots(nH, dx, n_snap, interval, seed, n_sites=16, first=4, growth=1.6,
+                   m_star=5.81e4 * MSUN):
+    """Star lists of snapshots 0..n_snap at times p * interval: a list of structured arrays
+    (fields STAR_FIELDS, cgs). Interval k (between snapshots k and k+1) forms
+    round(first * growth**k) stars at sites drawn among the n_sites highest peaks of nH."""
+    rng = np.random.default_rng(seed)
+    sites = density_peaks(nH, n_sites)
+    nz, ny, nx = nH.shape
+    born = []   # (birth time, x, y, z, lifetime, yield)
+    snaps = []
+    for p in range(n_snap + 1):
+        t_p = p * interval
+        rows = [(b[1], b[2], b[3], m_star, t_p - b[0], b[4], b[5]) for b in born]
+        snaps.append(np.array(rows, dtype=STAR_FIELDS))
+        if p == n_snap:
+            break
+        for _ in range(int(round(first * growth ** p))):
+            c = int(sites[rng.integers(len(sites))])
+            i, j, k = c % nx, (c // nx) % ny, c // (nx * ny)
+            off = rng.random(3)
+            born.append((t_p + rng.random() * interval, (i + off[0]) * dx, (j + off[1]) * dx,
+                         (k + off[2]) * dx, rng.uniform(5.0, 20.0) * MYR,
+                         rng.uniform(24000.0, 98000.0)))
+    return snaps
+
+
+def snapshot_workload(shape=(16, 20, 24), n_snap=3, steps_per_interval=40, seed_field=21,
+                      seed_stars=22, sigma_ln=1.5, dx_kpc=4.0):
+    """A small post-processing run: lognormal gas, a star-list sequence, the run parameters,
+    and the source-model parameters (escape fraction and boost of the 12.5 Mpc/h run, boost
+    evaluated at t = 500 Myr). The snapshot interval is steps_per_interval radiative steps."""
+    st, _, _, run = cosmo_box(None, sigma_ln, 1, seed_field, seed_field + 1, shape=shape,
+                              dx_kpc=dx_kpc)
+    interval = steps_per_interval * run["dt"]
+    snaps = star_snapshots(st["nH"], run["dx"], n_snap, interval, seed_stars)
+    model = dict(f_esc=0.055, boost_a=0.7, boost_k=300.0 * MYR, t0=500.0 * MYR)
+    return st, snaps, run, interval, model
