@@ -85,7 +85,21 @@ typedef struct {
                                   (section 3.2.1, Eq. 15, read with C_R on the
                                   recombination term and C_I on photo-ionisation) */
   double clump_I_A, clump_I_b; /* photo-ionisation clumping C_I = max(1, A nH^b); A = 0: off */
+  int flux;           /* intercell flux: ATON_FLUX_GLF (default) or ATON_FLUX_HLL */
 } aton_params;
+
+/* Intercell flux (section 2.2: the code offers Lax-Friedrichs and HLL; the paper uses LF).
+ * GLF: face flux (Phi_L + Phi_R)/2 - c (u_R - u_L)/2, wave speed c.
+ * HLL: (l+ Phi_L - l- Phi_R + l+ l- (u_R - u_L)) / (l+ - l-) with l- = min(0, lo_L, lo_R),
+ * l+ = max(0, hi_L, hi_R), lo/hi the extreme eigenvalues of the M1 flux Jacobian along the face
+ * normal in each cell: with chi(f), chi'(f) of the closure and mu the cosine between F and the
+ * normal, lo, hi = c (chi' mu -/+ sqrt((chi' mu)^2 - C)) / 2,
+ * C = (1 - mu^2)((3 chi - 1) chi' / f - 2) + 2 chi (1 - 3 mu^2) + 2 chi' f (3 mu^2 - 1)
+ * (the roots of the Jacobian's characteristic polynomial besides the transverse speed
+ * c (3 chi - 1) mu / (2 f); +-c/sqrt(3) at f = 0, c mu at f = 1). HLL runs through the plain
+ * (three-kernel) step whatever the execution mode. */
+#define ATON_FLUX_GLF 0
+#define ATON_FLUX_HLL 1
 
 /* Counters accumulated since aton_set_fields. */
 typedef struct {

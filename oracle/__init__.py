@@ -17,6 +17,8 @@ _LIBS = {}
 
 BC_PERIODIC = 0
 BC_TRANSMISSIVE = 1
+FLUX_GLF = 0
+FLUX_HLL = 1
 
 
 class Params(C.Structure):
@@ -28,6 +30,7 @@ class Params(C.Structure):
         ("T_floor", C.c_double), ("sub_eps", C.c_double), ("y_floor", C.c_double),
         ("clump_R_A", C.c_double), ("clump_R_b", C.c_double),
         ("clump_I_A", C.c_double), ("clump_I_b", C.c_double),
+        ("flux", C.c_int),
     ]
 
 
@@ -72,6 +75,8 @@ def lib(omp=False):
         L.orc_cell_step.restype = C.c_int
         L.orc_cell_step.argtypes = ([C.POINTER(Params)] + [_D] * 4 +
                                     [C.c_double] * 4 + [_D])
+        L.orc_m1_speeds.argtypes = [_D, C.c_double, C.c_int, _D, _D]
+        L.orc_m1_speeds.restype = None
         L.orc_stored.restype = C.c_double
         L.orc_stored.argtypes = [C.POINTER(Params), C.c_int64, _D]
         _LIBS[key] = L
@@ -101,6 +106,14 @@ def eddington(N, F, c):
     D = np.zeros(9)
     lib().orc_eddington(float(N), float(F[0]), float(F[1]), float(F[2]), float(c), _ptr(D))
     return D.reshape(3, 3)
+
+
+def m1_speeds(N, F, c, d):
+    """(lo, hi): extreme eigenvalues of the M1 flux Jacobian along axis d."""
+    u = np.array([N, F[0], F[1], F[2]], np.float64)
+    lo, hi = C.c_double(), C.c_double()
+    lib().orc_m1_speeds(_ptr(u), float(c), int(d), C.byref(lo), C.byref(hi))
+    return lo.value, hi.value
 
 
 def alpha_B(T):

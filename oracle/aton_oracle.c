@@ -161,6 +161,54 @@ static void orc_lf_flux(int d, const double uL[4], const double uR[4], double c,
   for (int q = 0; q < 4; ++q) out[q] = 0.5 * (fL[q] + fR[q]) - 0.5 * c * (uR[q] - uL[q]);
 }
 
+/* The HLL variant (section 2.2 names it beside LF): the wave speeds are the extreme eigenvalues
+ * of the Jacobian of the flux along d, G_d(u) = (F_d, c^2 N D_{x d}, c^2 N D_{y d}, c^2 N D_{z d}).
+ * With f = |F|/(cN), mu = F_d/|F| and the closure chi(f), its characteristic polynomial
+ * factors into the transverse root c (3 chi - 1) mu / (2 f) (twice) and the quadratic
+ * (lambda/c)^2 - chi' mu (lambda/c) + C/4 = 0, so
+ *   lambda/c = (chi' mu +- sqrt((chi' mu)^2 - C)) / 2,
+ *   C = (1 - mu^2)((3 chi - 1) chi'/f - 2) + 2 chi (1 - 3 mu^2) + 2 chi' f (3 mu^2 - 1),
+ * which bound the transverse pair. chi' is differentiated from the Levermore form in closed
+ * form here; at f = 0 (or N <= 0) the speeds are -+c/sqrt(3). */
+void orc_m1_speeds(const double u[4], double c, int d, double* lo, double* hi) {
+  const double N = u[0];
+  const double Fn = sqrt(u[1] * u[1] + u[2] * u[2] + u[3] * u[3]);
+  double f = (N > 0.0) ? Fn / (c * N) : 0.0;
+  if (f > 1.0) f = 1.0;
+  const double mu = (Fn > 0.0 && N > 0.0) ? u[1 + d] / Fn : 0.0;
+  const double s = sqrt(4.0 - 3.0 * f * f);
+  const double chi = (3.0 + 4.0 * f * f) / (5.0 + 2.0 * s);
+  /* d chi / d f = [8 f (5 + 2 s) + 6 f (3 + 4 f^2) / s] / (5 + 2 s)^2 */
+  const double dchi_over_f = (8.0 * (5.0 + 2.0 * s) + 6.0 * (3.0 + 4.0 * f * f) / s) /
+                             ((5.0 + 2.0 * s) * (5.0 + 2.0 * s));
+  const double three_chi_m1 = 3.0 * chi - 1.0;
+  const double C = (1.0 - mu * mu) * (three_chi_m1 * dchi_over_f - 2.0) +
+                   2.0 * chi * (1.0 - 3.0 * mu * mu) + 2.0 * dchi_over_f * f * f * (3.0 * mu * mu - 1.0);
+  const double b = dchi_over_f * f * mu;   /* chi' mu */
+  double disc = b * b - C;
+  if (disc < 0.0) disc = 0.0;
+  *lo = 0.5 * c * (b - sqrt(disc));
+  *hi = 0.5 * c * (b + sqrt(disc));
+}
+
+static void orc_hll_flux(int d, const double uL[4], const double uR[4], double c, double out[4]) {
+  double fL[4], fR[4], loL, hiL, loR, hiR;
+  orc_phys_flux(d, uL, c, fL);
+  orc_phys_flux(d, uR, c, fR);
+  orc_m1_speeds(uL, c, d, &loL, &hiL);
+  orc_m1_speeds(uR, c, d, &loR, &hiR);
+  double lm = loL < loR ? loL : loR;
+  double lp = hiL > hiR ? hiL : hiR;
+  if (lm > 0.0) lm = 0.0;
+  if (lp < 0.0) lp = 0.0;
+  if (lp - lm <= 0.0) {   /* both cells stream along the face: their fluxes along d vanish */
+    for (int q = 0; q < 4; ++q) out[q] = 0.5 * (fL[q] + fR[q]);
+    return;
+  }
+  for (int q = 0; q < 4; ++q)
+    out[q] = (lp * fL[q] - lm * fR[q] + lp * lm * (uR[q] - uL[q])) / (lp - lm);
+}
+
 /* neighbour index along d (step s = +1/-1) under the boundary condition; -1 marks "ghost of self" */
 static int64_t orc_nb(const orc_params* p, int nx, int ny, int nz, int i, int j, int k, int d, int s) {
   int n[3] = {nx, ny, nz};
@@ -195,8 +243,13 @@ void orc_transport(const orc_params* p, int nx, int ny, int nz,
           if (ip >= 0) { up[0] = N[ip]; up[1] = Fx[ip]; up[2] = Fy[ip]; up[3] = Fz[ip]; }
           if (im >= 0) { um[0] = N[im]; um[1] = Fx[im]; um[2] = Fy[im]; um[3] = Fz[im]; }
           double fp[4], fm[4];
-          orc_lf_flux(d, u, up, c, fp);   /* face i+1/2 */
-          orc_lf_flux(d, um, u, c, fm);   /* face i-1/2 */
+          if (p->flux == ORC_FLUX_HLL) {
+            orc_hll_flux(d, u, up, c, fp);
+            orc_hll_flux(d, um, u, c, fm);
+          } else {
+            orc_lf_flux(d, u, up, c, fp);   /* face i+1/2 */
+            orc_lf_flux(d, um, u, c, fm);   /* face i-1/2 */
+          }
           for (int q = 0; q < 4; ++q) acc[q] += fp[q] - fm[q];
           if (ip < 0) esc += fp[0] * face_dt;   /* outward through the high face */
           if (im < 0) esc -= fm[0] * face_dt;   /* outward through the low face */
@@ -427,8 +480,13 @@ int orc_cell_step(const orc_params* p, const double* N27, const double* Fx27, co
     double up[4] = {N27[ip], Fx27[ip], Fy27[ip], Fz27[ip]};
     double um[4] = {N27[im], Fx27[im], Fy27[im], Fz27[im]};
     double fp[4], fm[4];
-    orc_lf_flux(d, u, up, c, fp);
-    orc_lf_flux(d, um, u, c, fm);
+    if (p->flux == ORC_FLUX_HLL) {
+      orc_hll_flux(d, u, up, c, fp);
+      orc_hll_flux(d, um, u, c, fm);
+    } else {
+      orc_lf_flux(d, u, up, c, fp);
+      orc_lf_flux(d, um, u, c, fm);
+    }
     for (int q = 0; q < 4; ++q) acc[q] += fp[q] - fm[q];
   }
   double N = u[0] - lam * acc[0], Fx = u[1] - lam * acc[1], Fy = u[2] - lam * acc[2],

@@ -37,7 +37,11 @@ typedef struct {
   double y_floor;      /* floor of y in the sub-step criterion */
   double clump_R_A, clump_R_b;  /* recombination clumping C_R = max(1, A nH^b); A=0: C_R = 1 */
   double clump_I_A, clump_I_b;  /* photo-ionisation clumping C_I = max(1, A nH^b); A=0: C_I = 1 */
+  int flux;            /* ORC_FLUX_GLF (Lax-Friedrichs, speed c) or ORC_FLUX_HLL */
 } orc_params;
+
+#define ORC_FLUX_GLF 0
+#define ORC_FLUX_HLL 1
 
 /* Photon-budget accumulators [photons]; "stored" is computed on demand. */
 typedef struct {
@@ -54,6 +58,8 @@ void orc_default_params(orc_params* p);
 
 /* --- closure (section 2.2, Eqs. 5-6 and the chi paragraph) --- */
 double orc_chi(double f);
+/* extreme eigenvalues of the M1 flux Jacobian along axis d (0, 1, 2) for u = (N, Fx, Fy, Fz) */
+void orc_m1_speeds(const double u[4], double c, int d, double* lo, double* hi);
 void orc_eddington(double N, double Fx, double Fy, double Fz, double c, double D[9]);
 
 /* --- rates (fits from the literature the paper defers to; see the .c file) --- */

@@ -18,6 +18,7 @@ HOST, DEVICE = 0, 1
 BC_PERIODIC, BC_TRANSMISSIVE = 0, 1
 SRC_REPLACE, SRC_APPEND = 0, 1
 MODE_FUSED, MODE_UNFUSED, MODE_FUSED_LDG = 0, 1, 2
+FLUX_GLF, FLUX_HLL = 0, 1
 B_EMITTED, B_STORED, B_ABSORBED, B_ESCAPED, B_CLIPPED, B_STORED0 = range(6)
 BUDGET_LEN = 6
 BUDGET_KEYS = ("emitted", "stored", "absorbed", "escaped", "clipped", "stored0")
@@ -50,6 +51,7 @@ class aton_params(C.Structure):
         ("T_floor", C.c_double), ("sub_eps", C.c_double), ("y_floor", C.c_double),
         ("clump_R_A", C.c_double), ("clump_R_b", C.c_double),
         ("clump_I_A", C.c_double), ("clump_I_b", C.c_double),
+        ("flux", C.c_int),
     ]
 
 

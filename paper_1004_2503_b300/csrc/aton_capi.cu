@@ -136,6 +136,7 @@ static StepParams step_params(const aton_ctx* h) {
   P.y_floor = (float)h->prm.y_floor;
   P.clR_A = (float)h->prm.clump_R_A; P.clR_b = (float)h->prm.clump_R_b;
   P.clI_A = (float)h->prm.clump_I_A; P.clI_b = (float)h->prm.clump_I_b;
+  P.hll = h->prm.flux == ATON_FLUX_HLL;
   return P;
 }
 
@@ -288,7 +289,8 @@ static int enqueue_step(aton_handle h, cudaStream_t s) {
   const Fields in{h->f[h->cur][0], h->f[h->cur][1], h->f[h->cur][2], h->f[h->cur][3]};
   const Fields out{h->f[nxt][0], h->f[nxt][1], h->f[nxt][2], h->f[nxt][3]};
   cudaError_t e;
-  const bool plain_only = h->sink != nullptr || (h->sur && h->sur_p.enabled);
+  const bool plain_only = h->sink != nullptr || (h->sur && h->sur_p.enabled) ||
+                          h->prm.flux == ATON_FLUX_HLL;
   if (!plain_only && (h->mode == ATON_MODE_FUSED || h->mode == ATON_MODE_FUSED_LDG)) {
     FusedArgs a{};
     a.P = step_params(h);
@@ -618,6 +620,8 @@ int aton_set_params(aton_handle h, const aton_params* p) {
   if (!(p->clump_R_A >= 0) || !(p->clump_I_A >= 0) || !std::isfinite(p->clump_R_b) ||
       !std::isfinite(p->clump_I_b))
     return fail(ATON_ERR_BADARG, "clumping parameters out of range");
+  if (p->flux != ATON_FLUX_GLF && p->flux != ATON_FLUX_HLL)
+    return fail(ATON_ERR_BADARG, "flux must be ATON_FLUX_GLF or ATON_FLUX_HLL");
   h->prm = *p;
   drop_graphs(h);  // parameters are baked into captured launches
   return ATON_OK;
@@ -898,7 +902,8 @@ int aton_launches_per_step(aton_handle h, int* launches) {
   if (!launches) return fail(ATON_ERR_BADARG, "launches is NULL");
   if (h->mode == ATON_MODE_FUSED || h->mode == ATON_MODE_FUSED_LDG) *launches = 1;
   else *launches = h->src_n > 0 ? plain_launches() : plain_launches() - 1;
-  if ((h->sink || (h->sur && h->sur_p.enabled)) && *launches == 1)
+  if ((h->sink || (h->sur && h->sur_p.enabled) || h->prm.flux == ATON_FLUX_HLL) &&
+      *launches == 1)
     *launches = h->src_n > 0 ? plain_launches() : plain_launches() - 1;
   if (h->sur && h->sur_p.enabled) *launches += 1;   // the candidate pass (plus a counter reset)
   return ATON_OK;

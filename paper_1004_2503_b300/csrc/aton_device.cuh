@@ -23,6 +23,7 @@ struct StepParams {
   int fixed_T, coll_ion, cooling, max_sub;
   float T_floor, sub_eps, y_floor;
   float clR_A, clR_b, clI_A, clI_b;
+  int hll;             // intercell flux: 0 global Lax-Friedrichs, 1 HLL (plain step only)
 };
 
 // ---------------------------------------------------------------------------------------
@@ -81,6 +82,57 @@ __device__ __forceinline__ ND6 m1_pressure(float N, float fx, float fy, float fz
     r.xy = r.xz = r.yz = 0.f;
   }
   return r;
+}
+
+// ---------------------------------------------------------------------------------------
+// Extreme characteristic speeds (units of c) of the M1 flux Jacobian along an axis, the wave-
+// speed bounds of the HLL flux (section 2.2). With f = |Fh|/N, mu the cosine between Fh and the
+// axis, chi(f) and chi'(f) of the Levermore closure, the Jacobian's characteristic polynomial
+// has the transverse root (3 chi - 1) mu / (2 f) and the pair
+//   lambda = (chi' mu -/+ sqrt((chi' mu)^2 - C)) / 2,
+//   C = (1 - mu^2)((3 chi - 1) chi'/f - 2) + 2 chi (1 - 3 mu^2) + 2 chi' f (3 mu^2 - 1),
+// which bound all four (+-1/sqrt(3) at f = 0, mu at f = 1). Written without division by f:
+// chi'/f = (8 (5 + 2s) + 6 (3 + 4 f^2)/s) / (5 + 2s)^2 and 3 chi - 1 = f^2 (6/(2 + s) + 12)/(5 + 2s)
+// with s = sqrt(4 - 3 f^2), and chi' mu = (chi'/f) g_axis for g = Fh/N (g_axis = f mu).
+// ---------------------------------------------------------------------------------------
+struct M1Speeds {
+  float gx, gy, gz;   // Fh / N, |g| <= 1 (0 below kNTiny)
+  float f2;           // |g|^2
+  float chi, dcf, P1; // chi, chi'/f, (3 chi - 1) chi'/f - 2
+};
+
+__device__ __forceinline__ M1Speeds m1_speeds(float N, float fx, float fy, float fz) {
+  M1Speeds m;
+  m.gx = m.gy = m.gz = 0.f;
+  m.f2 = 0.f;
+  if (N > kNTiny) {
+    const float rN = rcp_fast(N);
+    m.gx = fx * rN; m.gy = fy * rN; m.gz = fz * rN;
+    m.f2 = m.gx * m.gx + m.gy * m.gy + m.gz * m.gz;
+    if (m.f2 > 1.f) {
+      const float k = rsqrtf(m.f2);
+      m.gx *= k; m.gy *= k; m.gz *= k;
+      m.f2 = 1.f;
+    }
+  }
+  const float s = sqrtf(4.f - 3.f * m.f2);          // in [1, 2]
+  const float r5 = rcp_fast(5.f + 2.f * s);
+  m.chi = (3.f + 4.f * m.f2) * r5;
+  m.dcf = fmaf(6.f * (3.f + 4.f * m.f2), rcp_fast(s), 8.f * (5.f + 2.f * s)) * r5 * r5;
+  const float tcm1 = m.f2 * fmaf(6.f, rcp_fast(2.f + s), 12.f) * r5;   // 3 chi - 1
+  m.P1 = tcm1 * m.dcf - 2.f;
+  return m;
+}
+
+// speeds along the axis whose component of g is gd
+__device__ __forceinline__ void m1_axis_speeds(const M1Speeds& m, float gd, float& lo, float& hi) {
+  const float mu2 = m.f2 > 1e-30f ? fminf(div_fast(gd * gd, m.f2), 1.f) : 0.f;
+  const float C = (1.f - mu2) * m.P1 + 2.f * m.chi * (1.f - 3.f * mu2) +
+                  2.f * m.dcf * m.f2 * (3.f * mu2 - 1.f);
+  const float b = m.dcf * gd;
+  const float r = sqrtf(fmaxf(b * b - C, 0.f));
+  lo = 0.5f * (b - r);
+  hi = 0.5f * (b + r);
 }
 
 // ---------------------------------------------------------------------------------------

@@ -188,7 +188,13 @@ __device__ __forceinline__ void load_u(const Fields& f, long long o, float rc, f
   u[3] = __ldg(f.Fz + o) * rc;
 }
 
-template <bool PER>
+// HLL face flux of one component: (l+ Phi_L - l- Phi_R + l+ l- (u_R - u_L)) / (l+ - l-)
+__device__ __forceinline__ float hll_face(float lm, float lp, float rd, float PL, float PR,
+                                          float uL, float uR) {
+  return (lp * PL - lm * PR + lp * lm * (uR - uL)) * rd;
+}
+
+template <bool PER, bool HLL>
 __global__ void __launch_bounds__(kPlainThreads) k_plain_transport(const PlainArgs A) {
   const StepParams& P = A.P;
   const int nx = P.nx, ny = P.ny, nz = P.nz;
@@ -202,6 +208,12 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain_transport(const PlainAr
     float u[4];
     load_u(A.in, id, P.rc, u);
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    ND6 dc{};
+    M1Speeds mc{};
+    if (HLL) {
+      dc = m1_pressure(u[0], u[1], u[2], u[3]);
+      mc = m1_speeds(u[0], u[1], u[2], u[3]);
+    }
     for (int d = 0; d < 3; ++d) {
       int ip[3] = {i, j, k}, im[3] = {i, j, k};
       ip[d] += 1; im[d] -= 1;
@@ -215,20 +227,50 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain_transport(const PlainAr
       load_u(A.in, om, P.rc, b);
       const ND6 da = m1_pressure(a[0], a[1], a[2], a[3]);
       const ND6 db = m1_pressure(b[0], b[1], b[2], b[3]);
-      float fa[4], fb[4];
+      float fa[4], fb[4], fc[4];
       if (d == 0) {
         fa[0] = a[1]; fa[1] = da.xx; fa[2] = da.xy; fa[3] = da.xz;
         fb[0] = b[1]; fb[1] = db.xx; fb[2] = db.xy; fb[3] = db.xz;
+        fc[0] = u[1]; fc[1] = dc.xx; fc[2] = dc.xy; fc[3] = dc.xz;
       } else if (d == 1) {
         fa[0] = a[2]; fa[1] = da.xy; fa[2] = da.yy; fa[3] = da.yz;
         fb[0] = b[2]; fb[1] = db.xy; fb[2] = db.yy; fb[3] = db.yz;
+        fc[0] = u[2]; fc[1] = dc.xy; fc[2] = dc.yy; fc[3] = dc.yz;
       } else {
         fa[0] = a[3]; fa[1] = da.xz; fa[2] = da.yz; fa[3] = da.zz;
         fb[0] = b[3]; fb[1] = db.xz; fb[2] = db.yz; fb[3] = db.zz;
+        fc[0] = u[3]; fc[1] = dc.xz; fc[2] = dc.yz; fc[3] = dc.zz;
       }
+      if (!HLL) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] += 0.5f * (fa[q] - fb[q]) - 0.5f * (a[q] - 2.f * u[q] + b[q]);
+        for (int q = 0; q < 4; ++q) acc[q] += 0.5f * (fa[q] - fb[q]) - 0.5f * (a[q] - 2.f * u[q] + b[q]);
+      } else {
+        // wave-speed bounds of the two faces from the three cells' speeds along d
+        const M1Speeds ma = m1_speeds(a[0], a[1], a[2], a[3]);
+        const M1Speeds mb = m1_speeds(b[0], b[1], b[2], b[3]);
+        const float gc = d == 0 ? mc.gx : (d == 1 ? mc.gy : mc.gz);
+        const float ga = d == 0 ? ma.gx : (d == 1 ? ma.gy : ma.gz);
+        const float gb = d == 0 ? mb.gx : (d == 1 ? mb.gy : mb.gz);
+        float lc, hc, la, ha, lb, hb;
+        m1_axis_speeds(mc, gc, lc, hc);
+        m1_axis_speeds(ma, ga, la, ha);
+        m1_axis_speeds(mb, gb, lb, hb);
+        const float lmp = fminf(0.f, fminf(lc, la)), lpp = fmaxf(0.f, fmaxf(hc, ha));   // face +
+        const float lmm = fminf(0.f, fminf(lb, lc)), lpm = fmaxf(0.f, fmaxf(hb, hc));   // face -
+        // l+ - l- >= 1/sqrt(3) unless both cells stream at f = 1 parallel to the face, where
+        // the two fluxes vanish: the guard then takes their mean
+        const float dp = lpp - lmp, dm = lpm - lmm;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float Fp = dp > 1e-6f ? hll_face(lmp, lpp, rcp_fast(dp), fc[q], fa[q], u[q], a[q])
+                                      : 0.5f * (fc[q] + fa[q]);
+          const float Fm = dm > 1e-6f ? hll_face(lmm, lpm, rcp_fast(dm), fb[q], fc[q], b[q], u[q])
+                                      : 0.5f * (fb[q] + fc[q]);
+          acc[q] += Fp - Fm;
+        }
+      }
     }
+    // acc is the sum over the three axes of (flux at the high face - flux at the low face)
     float Nn = u[0] - P.lam * acc[0];
     float Xn = u[1] - P.lam * acc[1];
     float Yn = u[2] - P.lam * acc[2];
@@ -431,8 +473,13 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain_chem_sur(const PlainArg
 int plain_launches() { return 3; }
 
 cudaError_t launch_plain_step(const PlainArgs& a, cudaStream_t s) {
-  if (a.P.bc == 0) k_plain_transport<true><<<kPlainBlocks, kPlainThreads, 0, s>>>(a);
-  else k_plain_transport<false><<<kPlainBlocks, kPlainThreads, 0, s>>>(a);
+  if (a.P.hll) {
+    if (a.P.bc == 0) k_plain_transport<true, true><<<kPlainBlocks, kPlainThreads, 0, s>>>(a);
+    else k_plain_transport<false, true><<<kPlainBlocks, kPlainThreads, 0, s>>>(a);
+  } else {
+    if (a.P.bc == 0) k_plain_transport<true, false><<<kPlainBlocks, kPlainThreads, 0, s>>>(a);
+    else k_plain_transport<false, false><<<kPlainBlocks, kPlainThreads, 0, s>>>(a);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (a.nsrc > 0) {

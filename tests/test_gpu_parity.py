@@ -324,3 +324,39 @@ def test_clumping_chemistry_matches_the_oracle(small, small_oracle, mode):
     assert b["absorbed"] == pytest.approx(ob["absorbed"], rel=1e-3)
     # the factors change the answer far beyond the gates
     assert np.abs(orc["x"] - small_oracle[0]["x"]).max() > 1e-2
+
+
+@pytest.mark.parametrize("mode", [A.MODE_FUSED, A.MODE_UNFUSED])
+def test_hll_flux_matches_the_oracle(small, small_oracle, mode):
+    """The HLL intercell flux (section 2.2) with the M1 wave-speed bounds: parity with the
+    oracle's HLL step; it runs through the plain step whatever the mode, and it differs from the
+    Lax-Friedrichs result well beyond the gates."""
+    st, idx, rate, run = small
+    orc, ob, _ = run_oracle(st, idx, rate, run, 100, flux=1)
+    a = A.from_workload(st, idx, rate, run, flux=A.FLUX_HLL)
+    a.set_exec(mode, 100)
+    assert a.launches_per_step() == 3
+    a.step(100)
+    assert a.synchronize() == 0
+    f = a.get_fields()
+    b = a.photon_budget()
+    a.close()
+    e = errors(f, orc)
+    print("hll errors", mode, e)
+    assert_gates(e, f"hll mode {mode}")
+    assert abs(budget_closure(b)) <= 1e-6
+    assert b["absorbed"] == pytest.approx(ob["absorbed"], rel=1e-3)
+    glf = small_oracle[0]
+    m = glf["N"] > 1e-6 * glf["N"].max()
+    assert np.max(np.abs(orc["N"][m] / glf["N"][m] - 1)) > 1e-2
+
+
+def test_hll_stromgren_transmissive_escape():
+    st, idx, rate, run = W.workload_32()
+    kw = dict(fixed_T=1, coll_ion=0)
+    orc, ob, _ = run_oracle(st, idx, rate, run, 100, flux=1, **kw)
+    f, b, d, rc = run_gpu(st, idx, rate, run, 100, flux=A.FLUX_HLL, **kw)
+    assert rc == 0
+    assert_gates(errors(f, orc))
+    assert abs(budget_closure(b)) <= 1e-6
+    assert b["escaped"] == pytest.approx(ob["escaped"], rel=1e-3, abs=1e-6 * ob["emitted"])
