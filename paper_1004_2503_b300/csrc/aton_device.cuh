@@ -203,11 +203,18 @@ struct ChemOut {
   int err;
 };
 
+// STD selects the standard configuration at compile time (evolving temperature with cooling
+// and collisional ionisation, no clumping), so its flag tests and clumping factors fold away;
+// the kernels take it when the step's parameters are that configuration.
+template <bool STD = false>
 __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float& N, float& fx,
                                              float& fy, float& fz, float& y, float& T) {
+  const bool fixedT = STD ? false : P.fixed_T != 0;
+  const bool cool = STD ? true : P.cooling != 0;
+  const bool coll = STD ? true : P.coll_ion != 0;
   float CR = 1.f, CI = 1.f;
-  if (P.clR_A > 0.f) CR = fmaxf(1.f, P.clR_A * exp2f(P.clR_b * log2f(n)));
-  if (P.clI_A > 0.f) CI = fmaxf(1.f, P.clI_A * exp2f(P.clI_b * log2f(n)));
+  if (!STD && P.clR_A > 0.f) CR = fmaxf(1.f, P.clR_A * exp2f(P.clR_b * log2f(n)));
+  if (!STD && P.clI_A > 0.f) CI = fmaxf(1.f, P.clI_A * exp2f(P.clI_b * log2f(n)));
   const float ksig = CI * P.csig;
   const float CRn = CR * n;
   // Remaining time as an unevaluated float pair rh + rl (error-free TwoSum updates): a plain
@@ -230,7 +237,7 @@ __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float
     const float l = kLog2TwoTHI - l2T;
     const float an = CRn * alpha_B(l);   // C_R alpha nH
     // the collisional rate is exactly 0 in FP32 below kTBetaMin, so it is not evaluated there
-    const float bn = (P.coll_ion && Tc > kTBetaMin) ? n * beta_coll(l, l2T, rT) : 0.f;
+    const float bn = (coll && Tc > kTBetaMin) ? n * beta_coll(l, l2T, rT) : 0.f;
     const float Gam = ksig * Nc;
     const float dydt = an * xi * xi - (Gam + bn * xi) * yc;
     float h = rem;
@@ -240,8 +247,8 @@ __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float
     // and finite)
     if (ady * h > P.sub_eps * ymax) h = div_fast(P.sub_eps * ymax, ady);
     float LK = 0.f;
-    if (!P.fixed_T) {
-      if (P.cooling) LK = cooling_K(Tc, l, l2T, rT, xi, yc, n, CR, P.coll_ion != 0);
+    if (!fixedT) {
+      if (cool) LK = cooling_K(Tc, l, l2T, rT, xi, yc, n, CR, coll);
       // gross rate: heating and cooling each bounded (no cancellation near thermal balance);
       // (heat + LK) / (1.5 (1 + x)) h <= eps T written without the quotient
       const float heat = Gam * yc * P.eheat_K;
@@ -294,7 +301,7 @@ __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float
     }
     Nh = fmaxf(Nh, 0.f);
     const float Nn = Nh + Nl;
-    if (!P.fixed_T) {
+    if (!fixedT) {
       // den >= 1.5 and bounded by the sub-step rule
       const float num = 1.5f * (1.f + xi) * Tc + div_fast(dN, n) * P.eheat_K;
       const float den = 1.5f * (2.f - Y) + h * LK * rT;

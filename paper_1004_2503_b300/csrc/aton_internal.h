@@ -88,6 +88,12 @@ struct PlainArgs {
   int* sur_count;       // number of candidates (reset before every chemistry pass)
 };
 
+// The standard chemistry configuration (evolving temperature, cooling and collisional
+// ionisation on, no clumping): the fused kernels have a compile-time instance for it.
+inline bool standard_chemistry(const StepParams& P) {
+  return !P.fixed_T && P.cooling && P.coll_ion && !(P.clR_A > 0.f) && !(P.clI_A > 0.f);
+}
+
 // ---- last-failure message of the calling thread (aton_capi.cu) ----
 void set_last_message(const char* msg);
 

@@ -25,7 +25,7 @@ namespace aton {
 // =========================================================================================
 // Fused step kernel
 // =========================================================================================
-template <int TY, bool PER>
+template <int TY, bool PER, bool STD>
 __global__ void __launch_bounds__(kTileX * TY) k_fused(const FusedArgs A) {
   constexpr int TX = kTileX, RX = kRingRX, PLR = RX * (TY + 2);
   constexpr int NH = 2 * TX + 2 * TY;
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused(const FusedArgs A) {
         src.z = nz;
         if (++sp < se) src = A.tsrc[sp];
       }
-      chem_tally_store(P, tl, cn, u, cy, cT, A.out, A.y, A.T, o);
+      chem_tally_store<STD>(P, tl, cn, u, cy, cT, A.out, A.y, A.T, o);
     }
     um = uc; pm = pc; uc = up; pc = pp;
     cy = ny_; cT = nT_; cn = nn_;
@@ -147,7 +147,11 @@ static constexpr size_t fused_smem() {
 
 template <int TY, bool PER>
 static cudaError_t set_fused_attr() {
-  return cudaFuncSetAttribute(k_fused<TY, PER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_fused<TY, PER, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)fused_smem<TY>());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_fused<TY, PER, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)fused_smem<TY>());
 }
 
@@ -166,7 +170,8 @@ static cudaError_t launch_fused_t(const FusedArgs& a, cudaStream_t s) {
   const size_t smem = fused_smem<TY>();
   dim3 grid((a.P.nx + kTileX - 1) / kTileX, (a.P.ny + TY - 1) / TY, (a.P.nz + a.tz - 1) / a.tz);
   dim3 block(kTileX, TY);
-  k_fused<TY, PER><<<grid, block, smem, s>>>(a);
+  if (standard_chemistry(a.P)) k_fused<TY, PER, true><<<grid, block, smem, s>>>(a);
+  else k_fused<TY, PER, false><<<grid, block, smem, s>>>(a);
   return cudaGetLastError();
 }
 

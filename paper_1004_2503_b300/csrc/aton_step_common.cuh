@@ -133,12 +133,13 @@ __device__ __forceinline__ float4 lf_update(const float4* U, const float4* Q, co
 }
 
 // Chemistry of the transported cell, its tallies and the store of the new state (physical F).
+template <bool STD>
 __device__ __forceinline__ void chem_tally_store(const StepParams& P, Tally& tl, float cn, float4 u,
                                                  float cy, float cT, const Fields& out, float* Yf,
                                                  float* Tf, long long o) {
   float Nn = u.x, Xn = u.y, Yn = u.z, Zn = u.w;
   const float N0 = Nn;
-  const ChemOut co = chem_cell(P, cn, Nn, Xn, Yn, Zn, cy, cT);
+  const ChemOut co = chem_cell<STD>(P, cn, Nn, Xn, Yn, Zn, cy, cT);
   tl.absorbed.add(N0 - Nn);
   tl.sub += co.nsub;
   tl.mx = max(tl.mx, (unsigned)co.nsub);

@@ -100,7 +100,7 @@ struct Layout {
 
 }  // namespace
 
-template <int TY, bool PER>
+template <int TY, bool PER, bool STD>
 __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
                                                            const __grid_constant__ TmaMaps M) {
   using L = Layout<TY>;
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
         if (++sp < se) src = A.tsrc[sp];
       }
       const float* C = stage0 + sk * L::STAGE + 4 * L::PLP + tid;
-      chem_tally_store(P, tl, C[2 * L::CH], u, C[0], C[L::CH], A.out, A.y, A.T, o);
+      chem_tally_store<STD>(P, tl, C[2 * L::CH], u, C[0], C[L::CH], A.out, A.y, A.T, o);
     }
     um = uc; pm = pc; uc = up; pc = pp;
     rk = rkn;
@@ -280,15 +280,20 @@ namespace {
 
 template <int TY, bool PER>
 cudaError_t set_tma_attr() {
-  return cudaFuncSetAttribute(k_fused_tma<TY, PER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)Layout<TY>::BYTES);
+  cudaError_t e = cudaFuncSetAttribute(k_fused_tma<TY, PER, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)Layout<TY>::BYTES);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_fused_tma<TY, PER, true>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Layout<TY>::BYTES);
 }
 
 template <int TY, bool PER>
 cudaError_t launch_tma_t(const FusedArgs& a, const TmaMaps& m, cudaStream_t s) {
   dim3 grid((a.P.nx + kTileX - 1) / kTileX, (a.P.ny + TY - 1) / TY, (a.P.nz + a.tz - 1) / a.tz);
   dim3 block(kTileX, TY);
-  k_fused_tma<TY, PER><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);
+  if (standard_chemistry(a.P)) k_fused_tma<TY, PER, true><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);
+  else k_fused_tma<TY, PER, false><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);
   return cudaGetLastError();
 }
 
