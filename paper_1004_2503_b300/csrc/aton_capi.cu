@@ -97,6 +97,7 @@ struct aton_ctx {
   aton_surrogate_params sur_p{};
   int* sur_list = nullptr;
   int* sur_count = nullptr;
+  double quiet_k = 0.0;   // rate bound of the chemistry's cold-gas shortcut (set with prm)
   // statistics pass
   float* st_edges = nullptr;
   double* st_part = nullptr;
@@ -114,6 +115,25 @@ static int check_h(aton_handle h) {
 static void drop_graphs(aton_handle h) {
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   h->graphs.clear();
+}
+
+// Upper bound over T in [T_floor, 1300 K] of alpha_B(T) and of the recombination plus free-free
+// cooling coefficients over 1.5 T (both / kB), with a 25 % margin over the maximum on a fine
+// grid: the kernels skip those rates in cold gas where this bound makes their effect on y and T
+// smaller than 2^-26 relatively.
+static double quiet_bound(double T_floor) {
+  double m = 0.0;
+  const double lo = std::log(T_floor), hi = std::log(1300.0);
+  for (int i = 0; i <= 4000; ++i) {
+    const double T = std::exp(lo + (hi - lo) * i / 4000.0);
+    const double lam = 2.0 * 157807.0 / T;
+    const double alpha = 2.753e-14 * std::pow(lam, 1.5) / std::pow(1.0 + std::pow(lam / 2.740, 0.407), 2.242);
+    const double rec = 3.435e-30 * T * std::pow(lam, 1.970) / std::pow(1.0 + std::pow(lam / 2.250, 0.376), 3.720);
+    const double d = std::log10(T) - 5.5;
+    const double ff = 1.42e-27 * (1.1 + 0.34 * std::exp(-d * d / 3.0)) * std::sqrt(T);
+    m = std::fmax(m, std::fmax(alpha, (rec + ff) / kKBh / (1.5 * T)));
+  }
+  return 1.25 * m;
 }
 
 static StepParams step_params(const aton_ctx* h) {
@@ -137,6 +157,7 @@ static StepParams step_params(const aton_ctx* h) {
   P.clR_A = (float)h->prm.clump_R_A; P.clR_b = (float)h->prm.clump_R_b;
   P.clI_A = (float)h->prm.clump_I_A; P.clI_b = (float)h->prm.clump_I_b;
   P.hll = h->prm.flux == ATON_FLUX_HLL;
+  P.quiet_k = (float)h->quiet_k;
   return P;
 }
 
@@ -562,6 +583,7 @@ int aton_init(int nx, int ny, int nz, double dx_cm, double c_cms, double dt_s, a
   h->nx = nx; h->ny = ny; h->nz = nz; h->ncell = ncell;
   h->dx = dx_cm; h->c = c_cms; h->dt = dt_s; h->V = dx_cm * dx_cm * dx_cm;
   aton_default_params(&h->prm);
+  h->quiet_k = quiet_bound(h->prm.T_floor);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) {
@@ -623,6 +645,7 @@ int aton_set_params(aton_handle h, const aton_params* p) {
   if (p->flux != ATON_FLUX_GLF && p->flux != ATON_FLUX_HLL)
     return fail(ATON_ERR_BADARG, "flux must be ATON_FLUX_GLF or ATON_FLUX_HLL");
   h->prm = *p;
+  h->quiet_k = quiet_bound(p->T_floor);
   drop_graphs(h);  // parameters are baked into captured launches
   return ATON_OK;
 }

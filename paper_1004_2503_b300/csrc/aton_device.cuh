@@ -24,6 +24,7 @@ struct StepParams {
   float T_floor, sub_eps, y_floor;
   float clR_A, clR_b, clI_A, clI_b;
   int hll;             // intercell flux: 0 global Lax-Friedrichs, 1 HLL (plain step only)
+  float quiet_k;       // bound of alpha_B(T) and (rec(T) + ff(T)) / (1.5 T), T_floor..kTExcMin
 };
 
 // ---------------------------------------------------------------------------------------
@@ -232,12 +233,20 @@ __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float
     }
     const float rem = rh;
     const float xi = 1.f - yc;
-    const float l2T = log2f(Tc);
-    const float rT = rcp_fast(Tc);   // T_floor <= Tc < FP32 max (validated input, floored update)
-    const float l = kLog2TwoTHI - l2T;
-    const float an = CRn * alpha_B(l);   // C_R alpha nH
-    // the collisional rate is exactly 0 in FP32 below kTBetaMin, so it is not evaluated there
-    const float bn = (coll && Tc > kTBetaMin) ? n * beta_coll(l, l2T, rT) : 0.f;
+    // Cold gas (below kTExcMin, where the collisional terms are exactly 0 in FP32) whose
+    // recombinations and cooling over the rest of the step would change y and T by less than
+    // 2^-26 relatively: those rates are not evaluated, their terms are below half an ulp of
+    // the float result (quiet_k bounds alpha_B(T) and (rec(T) + ff(T)) / (1.5 T) there).
+    const bool quiet = Tc < kTExcMin && rem * CRn * xi * xi * P.quiet_k <= 1.4901161e-8f * yc;
+    float l2T = 0.f, rT = 0.f, l = 0.f, an = 0.f, bn = 0.f;
+    if (!quiet) {
+      l2T = log2f(Tc);
+      rT = rcp_fast(Tc);   // T_floor <= Tc < FP32 max (validated input, floored update)
+      l = kLog2TwoTHI - l2T;
+      an = CRn * alpha_B(l);   // C_R alpha nH
+      // the collisional rate is exactly 0 in FP32 below kTBetaMin, so it is not evaluated there
+      bn = (coll && Tc > kTBetaMin) ? n * beta_coll(l, l2T, rT) : 0.f;
+    }
     const float Gam = ksig * Nc;
     const float dydt = an * xi * xi - (Gam + bn * xi) * yc;
     float h = rem;
@@ -248,7 +257,7 @@ __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float
     if (ady * h > P.sub_eps * ymax) h = div_fast(P.sub_eps * ymax, ady);
     float LK = 0.f;
     if (!fixedT) {
-      if (cool) LK = cooling_K(Tc, l, l2T, rT, xi, yc, n, CR, coll);
+      if (cool && !quiet) LK = cooling_K(Tc, l, l2T, rT, xi, yc, n, CR, coll);
       // gross rate: heating and cooling each bounded (no cancellation near thermal balance);
       // (heat + LK) / (1.5 (1 + x)) h <= eps T written without the quotient
       const float heat = Gam * yc * P.eheat_K;
