@@ -620,10 +620,8 @@ int aton_init(int nx, int ny, int nz, double dx_cm, double c_cms, double dt_s, a
   h->tz = std::min(64, nz);
   // TMA maps of the fields (row pitch must be a multiple of 16 bytes: nx % 4 == 0)
   {
-    float* chem[3] = {h->y, h->T, h->nH};
     const int tys[3] = {4, 8, 16};
-    for (int i = 0; i < 3; ++i)
-      h->tma_ok[i] = make_tma_maps(nx, ny, nz, tys[i], h->f, chem, &h->tma[i]);
+    for (int i = 0; i < 3; ++i) h->tma_ok[i] = make_tma_maps(nx, ny, nz, tys[i], h->f, &h->tma[i]);
   }
   *out = h;
   return ATON_OK;

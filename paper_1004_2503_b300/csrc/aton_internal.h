@@ -43,7 +43,6 @@ struct Slots {
 // Tensor maps of the TMA-staged fused kernel (one set per tile height).
 struct TmaMaps {
   CUtensorMap u[2][4];   // ping-pong buffer x (N, Fx, Fy, Fz), box (32+8) x (ty+2) x 1
-  CUtensorMap chem[3];   // y, T, nH, box 32 x ty x 1
 };
 
 struct Fields {
@@ -101,8 +100,7 @@ void set_last_message(const char* msg);
 cudaError_t init_kernel_attributes();
 cudaError_t init_tma_attributes();
 cudaError_t launch_fused_tma(int ty, const FusedArgs& a, const TmaMaps& m, cudaStream_t s);
-bool make_tma_maps(int nx, int ny, int nz, int ty, float* const u[2][4], float* const chem[3],
-                   TmaMaps* out);
+bool make_tma_maps(int nx, int ny, int nz, int ty, float* const u[2][4], TmaMaps* out);
 cudaError_t launch_fused(int ty, const FusedArgs& a, cudaStream_t s);
 int fused_tiles(int nx, int ny, int nz, int ty, int tz);
 cudaError_t launch_plain_step(const PlainArgs& a, cudaStream_t s);

@@ -4,10 +4,11 @@
 // sources, section 2.3; chemistry operator Phi, Appendix Eq. A4), with the plane loads moved
 // to the TMA engine. Thread 0 streams each z-plane of the CTA's 32 x TY column tile into a
 // three-deep shared-memory stage ring with cp.async.bulk.tensor: a (32+8) x (TY+2) box of each
-// of N, Fx, Fy, Fz (one-cell halo; the x origin is 4 cells left so it stays 16-byte aligned)
-// and a 32 x TY box of y, T, nH; one mbarrier per stage signals the landed bytes. A stage is
-// refilled right after the CTA barrier that ends its last use, so no thread waits on a free
-// stage and no warp is spent on producing. Every thread turns each landed plane into a
+// of N, Fx, Fy, Fz (one-cell halo; the x origin is 4 cells left so it stays 16-byte aligned);
+// one mbarrier per stage signals the landed bytes. A stage is refilled right after the CTA
+// barrier that ends its use, three planes ahead of the next use, so no thread waits on a free
+// stage and no warp is spent on producing. The chemistry fields y, T, nH of the own cell are
+// loaded one plane ahead into registers. Every thread turns each landed plane into a
 // three-plane ring of vector records per slot, (N, F/c), (Dxx, Dxy, Dxz, Dyy) N and
 // (Dyz, Dzz) N, patching the slots that lie outside the grid from global memory (boundary
 // map; edge tiles only) and computing N D once per slot; a neighbour then costs two or three
@@ -26,7 +27,7 @@ namespace aton {
 
 namespace {
 
-constexpr int kStages = 3;   // a stage is refilled two planes ahead of its use
+constexpr int kStages = 3;   // planes in flight: a stage is refilled three planes ahead
 constexpr int kBoxX = kTileX + 8;          // x0-4 .. x0+35
 constexpr unsigned kWaitLimit = 1u << 26;            // polls before a wait is declared failed
 constexpr unsigned long long kWaitNs = 2000000000ull;  // or nanoseconds (2 s), whichever first
@@ -87,12 +88,10 @@ template <int TY>
 struct Layout {
   static constexpr int PL = kBoxX * (TY + 2);             // floats per field-plane (with halo)
   static constexpr int PLP = (PL + 31) & ~31;             // padded to 128 bytes
-  static constexpr int CH = kTileX * TY;                  // chemistry box floats
-  static constexpr int STAGE = 4 * PLP + 3 * CH;          // floats per stage
+  static constexpr int STAGE = 4 * PLP;                  // floats per stage
   static constexpr int RX = kTileX + 2;                   // ring row pitch (one-cell halo)
   static constexpr int PLR = RX * (TY + 2);               // ring slots per plane
   static constexpr unsigned U_BYTES = 4u * PL * 4u;       // bytes landed per plane (u)
-  static constexpr unsigned C_BYTES = 3u * CH * 4u;       // bytes landed per plane (chem)
   static constexpr size_t STAGE_BYTES = (size_t)kStages * STAGE * 4;
   static constexpr size_t RING_BYTES = (size_t)3 * PLR * (16 + 16 + 8);
   static constexpr size_t BYTES = STAGE_BYTES + RING_BYTES + kStages * 8 + 128;
@@ -132,14 +131,10 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
   auto issue = [&](int k) {
     const int s = k % kStages;
     const int p = plane_of(z0 - 1 + k);
-    const bool chem = k >= 1 && k <= z1 - z0;
-    mbar_expect_tx(&full[s], L::U_BYTES + (chem ? L::C_BYTES : 0u));
+    mbar_expect_tx(&full[s], L::U_BYTES);
     float* st = stage0 + s * L::STAGE;
     for (int q = 0; q < 4; ++q)
       tma_load_3d(st + q * L::PLP, &M.u[A.in_buf][q], x0 - 4, y0 - 1, p, &full[s]);
-    if (chem)
-      for (int q = 0; q < 3; ++q)
-        tma_load_3d(st + 4 * L::PLP + q * L::CH, &M.chem[q], x0, y0, p, &full[s]);
   };
   auto wait = [&](int k) {   // plane k landed (skipped once a wait has failed)
     if (!failed && !mbar_wait(&full[k % kStages], (k / kStages) & 1)) failed = true;
@@ -216,9 +211,11 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
   TileSrc src{nz, 0, 0.f, 0};
   if (sp < se) src = A.tsrc[sp];
   long long o = (long long)z0 * plane + ocol;
+  float cy = 0.f, cT = 1.f, cn = 1.f;
+  if (act) { cy = A.y[o]; cT = A.T[o]; cn = __ldg(A.nH + o); }
   int rk = 1, rkn = 2;                  // ring planes of z and z+1 (plane index mod 3)
   // stages of z and z+1 (plane index mod kStages) and the phase parity of the latter
-  int sk = 1 % kStages, skn = 2 % kStages;
+  int skn = 2 % kStages;
   unsigned pkn = (2 / kStages) & 1;
 
   for (int z = z0; z < z1; ++z, o += plane) {
@@ -232,12 +229,15 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
       pp = put(rkn, orslot, up);
       if (hslot >= 0) put(rkn, hrslot, prep(st, hslot, halo_out, hcol, p));
     }
+    // chemistry fields of the own cell, one plane ahead
+    float ny_ = 0.f, nT_ = 1.f, nn_ = 1.f;
+    if (act && z + 1 < z1) { ny_ = A.y[o + plane]; nT_ = A.T[o + plane]; nn_ = __ldg(A.nH + o + plane); }
     __syncthreads();
-    // every thread is done with plane k-1 (its box read for the ring, its chemistry fields
-    // read by the cell updates): its stage takes plane k-1+kStages
-    if (tid == 0 && !failed && k - 1 + kStages < nplanes) {
+    // every thread has turned plane k+1 into ring records (before this barrier), so the stages
+    // of planes up to k+1 are free: keep planes k+2 .. k+1+kStages in flight
+    if (tid == 0 && !failed && issued < nplanes && issued <= k + 1 + kStages) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(issued++);
+      while (issued < nplanes && issued <= k + 1 + kStages) issue(issued++);
     }
     if (act) {
       const int c0 = rk * L::PLR + orslot;
@@ -258,13 +258,12 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
         src.z = nz;
         if (++sp < se) src = A.tsrc[sp];
       }
-      const float* C = stage0 + sk * L::STAGE + 4 * L::PLP + tid;
-      chem_tally_store<STD>(P, tl, C[2 * L::CH], u, C[0], C[L::CH], A.out, A.y, A.T, o);
+      chem_tally_store<STD>(P, tl, cn, u, cy, cT, A.out, A.y, A.T, o);
     }
     um = uc; pm = pc; uc = up; pc = pp;
+    cy = ny_; cT = nT_; cn = nn_;
     rk = rkn;
     rkn = rkn == 2 ? 0 : rkn + 1;
-    sk = skn;
     if (++skn == kStages) { skn = 0; pkn ^= 1u; }
   }
   if (failed) atomicAdd(A.slots.timeout, 1u);
@@ -319,11 +318,10 @@ cudaError_t launch_fused_tma(int ty, const FusedArgs& a, const TmaMaps& m, cudaS
   }
 }
 
-// Tensor maps of the grid fields for a tile height ty: for each ping-pong buffer and each of
-// N, Fx, Fy, Fz a (32+8) x (ty+2) x 1 box, and 32 x ty x 1 boxes of y, T, nH. Returns false if
-// the driver entry point is unavailable or an encode fails (the caller then uses k_fused).
-bool make_tma_maps(int nx, int ny, int nz, int ty, float* const u[2][4], float* const chem[3],
-                   TmaMaps* out) {
+// Tensor maps of the radiation fields for a tile height ty: for each ping-pong buffer and each
+// of N, Fx, Fy, Fz a (32+8) x (ty+2) x 1 box. Returns false if the driver entry point is
+// unavailable or an encode fails (the caller then uses k_fused).
+bool make_tma_maps(int nx, int ny, int nz, int ty, float* const u[2][4], TmaMaps* out) {
   if (nx % 4 != 0) return false;
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
@@ -339,7 +337,6 @@ bool make_tma_maps(int nx, int ny, int nz, int ty, float* const u[2][4], float* 
   const cuuint64_t strides[2] = {(cuuint64_t)nx * 4, (cuuint64_t)nx * ny * 4};
   const cuuint32_t estr[3] = {1, 1, 1};
   const cuuint32_t box_u[3] = {(cuuint32_t)kBoxX, (cuuint32_t)(ty + 2), 1};
-  const cuuint32_t box_c[3] = {(cuuint32_t)kTileX, (cuuint32_t)ty, 1};
   for (int b = 0; b < 2; ++b)
     for (int q = 0; q < 4; ++q)
       if (encode(&out->u[b][q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, u[b][q], dims, strides, box_u,
@@ -347,12 +344,6 @@ bool make_tma_maps(int nx, int ny, int nz, int ty, float* const u[2][4], float* 
                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
           CUDA_SUCCESS)
         return false;
-  for (int q = 0; q < 3; ++q)
-    if (encode(&out->chem[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, chem[q], dims, strides, box_c,
-               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
-        CUDA_SUCCESS)
-      return false;
   return true;
 }
 
