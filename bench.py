@@ -113,6 +113,10 @@ def workload(grid):
         return W.workload_512(), ("lognormal n_H (sigma_ln=2.0, P(k)~k^-2.5, seed 3), 4096 sources "
                                   "at the highest peaks (log-uniform 1e50-1e52 /s, seed 4), "
                                   "dx=4 kpc, periodic, T0=100 K, x0=1e-4")
+    if grid == 1024:
+        return W.workload_1024(), ("lognormal n_H (sigma_ln=2.0, P(k)~k^-2.5, seed 5), 32768 "
+                                   "sources at the highest peaks (log-uniform 1e50-1e52 /s, seed "
+                                   "6), dx=4 kpc, periodic, T0=100 K, x0=1e-4, float32 state")
     st = W.cosmo_box(grid, 2.0, max(1, 4096 * grid ** 3 // 512 ** 3), 3, 4)
     return st, f"lognormal {grid}^3 (sigma_ln=2.0), scaled source count"
 
@@ -264,15 +268,43 @@ def ours(args, world, rank, local):
     clocks = Clocks(local)
     barrier()
     clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    a.step(args.steps)
-    e1.record(stream)
-    e1.synchronize()
-    barrier()
-    clk = clocks.stop()
-    t = maxtime(e0.elapsed_time(e1) / 1e3)
+    history = []
+    if args.history > 0:
+        # timed in chunks of `history` steps; the statistics between chunks are not timed
+        t_dev = 0.0
+        done = 0
+        while done < args.steps:
+            k = min(args.history, args.steps - done)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            a.step(k)
+            e1.record(stream)
+            e1.synchronize()
+            t_dev += e0.elapsed_time(e1) / 1e3
+            done += k
+            s = a.ionisation_stats()
+            bb = a.photon_budget()
+            history.append({"step": args.warmup + done, "x_volume": s["x_volume"],
+                            "x_mass": s["x_mass"], "J21_volume": s["J21_volume"],
+                            "T_volume": s["T_volume"],
+                            "budget_closure": (bb["stored0"] + bb["emitted"] - bb["stored"] -
+                                               bb["absorbed"] - bb["escaped"] - bb["clipped"]) /
+                            max(bb["emitted"], 1e-300)})
+        barrier()
+        clk = clocks.stop()
+        t = maxtime(t_dev)
+        args.history_records = history
+    else:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        a.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+        barrier()
+        clk = clocks.stop()
+        t = maxtime(e0.elapsed_time(e1) / 1e3)
     rc = a.synchronize()
     diag = a.diag()
     bud = a.photon_budget()
@@ -355,7 +387,7 @@ def finish(args, world, rank, dist, st, idx, rate, run, desc, ncell, value, ms, 
         "config": {"workload": desc, "grid": args.grid, "cells": ncell, "sources": len(idx),
                    "mode": kernel, "graph_batch": args.graph_batch, "tile_ty_tz": [ty, tz],
                    "autotune_ms_per_step": tune_ms, "parallelism": f"replicas x{world}",
-                   "l2": "no flush: 7.0 GB of state per step >> 126 MB L2"},
+                   "l2": f"no flush: {44 * ncell / 1e9:.1f} GB of state per step >> 126 MB L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_kind,
                      "traffic": None if traffic is None else traffic * ncell,
@@ -366,6 +398,7 @@ def finish(args, world, rank, dist, st, idx, rate, run, desc, ncell, value, ms, 
         "gpu_launches": launches,
         "clocks": clk,
         "status": rc,
+        "history": getattr(args, "history_records", None) or None,
         "diag": diag,
         "budget_closure": (bud["stored0"] + bud["emitted"] - bud["stored"] - bud["absorbed"] -
                            bud["escaped"] - bud["clipped"]) / max(bud["emitted"], 1e-300),
@@ -395,6 +428,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--grid", type=int, default=512)
     ap.add_argument("--graph-batch", type=int, default=100)
+    ap.add_argument("--history", type=int, default=0,
+                    help="time in chunks of this many steps and record the ionised fraction, "
+                         "J21, T and the budget after each chunk (statistics not timed)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-unfused", action="store_true")

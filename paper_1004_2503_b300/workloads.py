@@ -111,6 +111,40 @@ def cosmo_box(n, sigma_ln, nsrc, seed_field, seed_src, mean_nH=2e-4, T0=100.0, x
     return st, idx, rate, run
 
 
+def cosmo_box_f32(n, sigma_ln, nsrc, seed_field, seed_src, mean_nH=2e-4, T0=100.0, x0=1e-4,
+                  dx_kpc=4.0, lum=(1e50, 1e52), c=C_LIGHT):
+    """The lognormal recipe of cosmo_box with the state built in float32 and the field's
+    intermediates released early (for 1024^3, where float64 copies of seven fields would take
+    60 GB of host memory). The Gaussian field is the same one cosmo_box draws."""
+    nz = ny = nx = n
+    rng = np.random.default_rng(seed_field)
+    wk = np.fft.rfftn(rng.standard_normal((nz, ny, nx), dtype=np.float64))
+    for k in range(nz):   # P(k) ~ k^-2.5 amplitude, one plane at a time
+        kz = np.fft.fftfreq(nz)[k]
+        k2 = kz * kz + np.fft.fftfreq(ny)[:, None] ** 2 + np.fft.rfftfreq(nx)[None, :] ** 2
+        if k == 0:
+            k2[0, 0] = 1.0
+        amp = k2 ** (-2.5 / 4.0)
+        if k == 0:
+            amp[0, 0] = 0.0
+        wk[k] *= amp
+    g = np.fft.irfftn(wk, s=(nz, ny, nx), axes=(0, 1, 2))
+    del wk
+    g -= g.mean()
+    g /= g.std()
+    nH = (mean_nH * np.exp(sigma_ln * g - 0.5 * sigma_ln * sigma_ln)).astype(np.float32)
+    del g
+    z = np.zeros_like(nH)
+    st = dict(N=z, Fx=np.zeros_like(nH), Fy=np.zeros_like(nH), Fz=np.zeros_like(nH),
+              x=np.full_like(nH, x0), T=np.full_like(nH, T0), nH=nH)
+    idx = density_peaks(nH, nsrc)
+    rate = loguniform_rates(nsrc, lum[0], lum[1], seed_src)
+    dx = dx_kpc * KPC
+    run = dict(nx=nx, ny=ny, nz=nz, dx=dx, c=c, dt=cfl_dt(dx, c), bc="periodic",
+               sigma_n=SIGMA, sigma_e=SIGMA, e_gamma_eV=E_GAMMA_EV)
+    return st, idx, rate, run
+
+
 # The workloads, by grid size. Each returns (state, src_idx, src_rate, run_params).
 def workload_32():
     return stromgren_box()
@@ -122,6 +156,10 @@ def workload_128(seed_field=1, seed_src=2):
 
 def workload_512(seed_field=3, seed_src=4):
     return cosmo_box(512, 2.0, 4096, seed_field, seed_src)
+
+
+def workload_1024(seed_field=5, seed_src=6):
+    return cosmo_box_f32(1024, 2.0, 32768, seed_field, seed_src)
 
 
 def workload_256(seed_field=10, seed_src=11):

@@ -51,3 +51,39 @@ def test_512_sampled_cells_match_the_oracle_step(w512):
             worst["N"] = max(worst["N"], abs(float(cur["N"][k, j, i]) - r["N"]) / r["N"])
     print("512^3 sampled worst", worst, "cells", len(sample))
     assert worst["x"] <= 1e-3 and worst["T"] <= 1e-3 and worst["N"] <= 1e-3, worst
+
+
+def test_1024_sampled_cells_match_the_oracle_step():
+    """The 1024^3 workload (43 GB of float32 state on the device): one step of sampled cells
+    against the oracle, after 10 steps in the benchmark's launch configuration."""
+    st, idx, rate, run = W.workload_1024()
+    shape = st["N"].shape
+    a = A.from_workload(st, idx, rate, run)
+    a.autotune(1)
+    a.set_exec(a.get_exec()["mode"], 100)
+    a.step(10)
+    prev = a.get_fields()
+    a.step(1)
+    assert a.synchronize() == 0
+    cur = a.get_fields()
+    b = a.photon_budget()
+    a.close()
+    clos = (b["stored0"] + b["emitted"] - b["stored"] - b["absorbed"] - b["escaped"] -
+            b["clipped"]) / b["emitted"]
+    assert abs(clos) <= 1e-6
+    p = oracle_params(run)
+    src = dict(zip(idx.tolist(), rate.tolist()))
+    rng = np.random.default_rng(1)
+    hot = np.argpartition(prev["N"].ravel(), -64)[-64:]
+    sample = np.unique(np.concatenate([idx[:64], hot, rng.choice(prev["N"].size, 128, replace=False)]))
+    worst = dict(x=0.0, T=0.0, N=0.0)
+    for cell in sample:
+        nb, (k, j, i) = neighbourhood(prev, cell, shape, periodic=True)
+        r = O.cell_step(p, nb["N"], nb["Fx"], nb["Fy"], nb["Fz"], float(prev["x"][k, j, i]),
+                        float(prev["T"][k, j, i]), float(st["nH"][k, j, i]), src.get(int(cell), 0.0))
+        worst["x"] = max(worst["x"], abs(float(cur["x"][k, j, i]) - r["x"]))
+        worst["T"] = max(worst["T"], abs(float(cur["T"][k, j, i]) - r["T"]) / r["T"])
+        if r["N"] > 1e-6 * float(prev["N"].max()):
+            worst["N"] = max(worst["N"], abs(float(cur["N"][k, j, i]) - r["N"]) / r["N"])
+    print("1024^3 sampled worst", worst, "cells", len(sample))
+    assert worst["x"] <= 1e-3 and worst["T"] <= 1e-3 and worst["N"] <= 1e-3, worst
