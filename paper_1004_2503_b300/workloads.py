@@ -116,9 +116,12 @@ def cosmo_box_f32(n, sigma_ln, nsrc, seed_field, seed_src, mean_nH=2e-4, T0=100.
     """The lognormal recipe of cosmo_box with the state built in float32 and the field's
     intermediates released early (for 1024^3, where float64 copies of seven fields would take
     60 GB of host memory). The Gaussian field is the same one cosmo_box draws."""
+    import os
+    from scipy import fft as sfft
+    workers = os.cpu_count() or 1
     nz = ny = nx = n
     rng = np.random.default_rng(seed_field)
-    wk = np.fft.rfftn(rng.standard_normal((nz, ny, nx), dtype=np.float64))
+    wk = sfft.rfftn(rng.standard_normal((nz, ny, nx), dtype=np.float64), workers=workers)
     for k in range(nz):   # P(k) ~ k^-2.5 amplitude, one plane at a time
         kz = np.fft.fftfreq(nz)[k]
         k2 = kz * kz + np.fft.fftfreq(ny)[:, None] ** 2 + np.fft.rfftfreq(nx)[None, :] ** 2
@@ -128,7 +131,7 @@ def cosmo_box_f32(n, sigma_ln, nsrc, seed_field, seed_src, mean_nH=2e-4, T0=100.
         if k == 0:
             amp[0, 0] = 0.0
         wk[k] *= amp
-    g = np.fft.irfftn(wk, s=(nz, ny, nx), axes=(0, 1, 2))
+    g = sfft.irfftn(wk, s=(nz, ny, nx), axes=(0, 1, 2), workers=workers)
     del wk
     g -= g.mean()
     g /= g.std()
