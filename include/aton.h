@@ -109,6 +109,8 @@ typedef struct {
   int64_t error_cells;      /* cell-steps that reached the sub-cycle cap */
   int64_t nonfinite_cells;  /* cell-steps that produced a non-finite value */
   int64_t surrogate_cells;  /* cell-steps whose chemistry the surrogate replaced */
+  double max_f;             /* largest reduced flux |F|/(cN) of the current state (cells with
+                               N > 1e-30; the M1 closure of section 2.2 needs f <= 1) */
 } aton_diag;
 
 /* Chemistry surrogate in the step (see aton_set_surrogate). */

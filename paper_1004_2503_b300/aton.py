@@ -58,7 +58,8 @@ class aton_params(C.Structure):
 class aton_diag(C.Structure):
     _fields_ = [("steps", C.c_int64), ("substeps_total", C.c_int64),
                 ("substeps_max", C.c_int64), ("error_cells", C.c_int64),
-                ("nonfinite_cells", C.c_int64), ("surrogate_cells", C.c_int64)]
+                ("nonfinite_cells", C.c_int64), ("surrogate_cells", C.c_int64),
+                ("max_f", C.c_double)]
 
 
 class aton_surrogate_params(C.Structure):

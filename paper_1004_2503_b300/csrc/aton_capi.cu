@@ -906,6 +906,17 @@ int aton_get_diag(aton_handle h, aton_diag* out) {
   out->substeps_max = (int64_t)u[1];
   out->error_cells = (int64_t)u[2];
   out->nonfinite_cells = (int64_t)u[3];
+  // largest reduced flux of the current state (a reduction over N, F on demand)
+  cudaStream_t s = h->stream();
+  CU(cudaMemsetAsync(h->d_bad, 0, sizeof(unsigned int), s));
+  CU(launch_max_f2(h->f[h->cur][0], h->f[h->cur][1], h->f[h->cur][2], h->f[h->cur][3],
+                   (float)(1.0 / h->c), h->ncell, h->d_bad, s));
+  unsigned int bits = 0;
+  CU(cudaMemcpyAsync(&bits, h->d_bad, sizeof(bits), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  float f2;
+  std::memcpy(&f2, &bits, sizeof(f2));
+  out->max_f = std::sqrt((double)f2);
   return ATON_OK;
 }
 

@@ -108,6 +108,8 @@ const MlpImage* mlp_image(const struct ::aton_mlp* h);
 const MlpNorm* mlp_norm(const struct ::aton_mlp* h);
 int plain_launches();
 cudaError_t launch_scale(float* dst, const float* src, float k, int64_t n, cudaStream_t s);
+cudaError_t launch_max_f2(const float* N, const float* Fx, const float* Fy, const float* Fz,
+                          float rc, int64_t n, unsigned int* out, cudaStream_t s);
 cudaError_t launch_one_minus(float* dst, const float* src, int64_t n, cudaStream_t s);
 cudaError_t launch_validate(const float* N, const float* y, const float* T, const float* nH,
                             int64_t n, unsigned int* bad, cudaStream_t s);

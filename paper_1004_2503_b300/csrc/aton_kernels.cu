@@ -533,6 +533,30 @@ __global__ void k_validate(const float* N, const float* y, const float* T, const
   if (b) atomicAdd(bad, b);
 }
 
+// Largest f^2 = |F|^2 / (cN)^2 of a state (cells with N > kNTiny), as the bits of a float:
+// non-negative floats order like their bit patterns, so an integer atomicMax finds it.
+__global__ void k_max_f2(const float* N, const float* Fx, const float* Fy, const float* Fz,
+                         float rc, long long n, unsigned int* out) {
+  float m = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float a = __ldg(N + i);
+    if (a > kNTiny) {
+      const float x = __ldg(Fx + i) * rc, y = __ldg(Fy + i) * rc, z = __ldg(Fz + i) * rc;
+      m = fmaxf(m, div_fast(x * x + y * y + z * z, a * a));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(out, __float_as_uint(m));
+}
+
+cudaError_t launch_max_f2(const float* N, const float* Fx, const float* Fy, const float* Fz,
+                          float rc, int64_t n, unsigned int* out, cudaStream_t s) {
+  k_max_f2<<<148 * 4, 256, 0, s>>>(N, Fx, Fy, Fz, rc, n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_scale(float* dst, const float* src, float k, int64_t n, cudaStream_t s) {
   k_scale<<<148 * 4, 256, 0, s>>>(dst, src, k, n);
   return cudaGetLastError();

@@ -360,3 +360,34 @@ def test_hll_stromgren_transmissive_escape():
     assert_gates(errors(f, orc))
     assert abs(budget_closure(b)) <= 1e-6
     assert b["escaped"] == pytest.approx(ob["escaped"], rel=1e-3, abs=1e-6 * ob["emitted"])
+
+
+@pytest.mark.parametrize("mode", [A.MODE_FUSED, A.MODE_UNFUSED])
+def test_largest_reduced_flux_is_reported(mode):
+    """aton_diag.max_f: the largest |F|/(cN) of the current state, the realisability bound
+    f <= 1 of the M1 closure (section 2.2), on a state streaming at up to f = 0.97."""
+    st, idx, rate, run = W.workload_small(shape=(12, 16, 20), nsrc=2)
+    rng = np.random.default_rng(5)
+    shape = st["N"].shape
+    N = rng.uniform(1e-6, 1e-3, shape)
+    f = rng.uniform(0.0, 0.97, shape)
+    n = rng.normal(size=(3,) + shape)
+    n /= np.linalg.norm(n, axis=0)
+    c = run["c"]
+    st = dict(st, N=N, Fx=c * N * f * n[0], Fy=c * N * f * n[1], Fz=c * N * f * n[2])
+    a = A.from_workload(st, idx, rate, run)
+    a.set_exec(mode, 0)
+    d0 = a.diag()
+    a.step(3)
+    assert a.synchronize() == 0
+    d = a.diag()
+    g = a.get_fields()
+    a.close()
+    N32 = st["N"].astype(np.float32).astype(np.float64)
+    F32 = [st[k].astype(np.float32).astype(np.float64) for k in ("Fx", "Fy", "Fz")]
+    assert d0["max_f"] == pytest.approx((np.sqrt(sum(x * x for x in F32)) / (c * N32)).max(),
+                                        rel=1e-5)
+    Ng = g["N"].astype(np.float64)
+    fg = np.sqrt(sum(g[k].astype(np.float64) ** 2 for k in ("Fx", "Fy", "Fz"))) / (c * Ng)
+    assert d["max_f"] == pytest.approx(fg[Ng > 1e-30].max(), rel=1e-5)
+    assert d["max_f"] <= 1.0 + 1e-6
