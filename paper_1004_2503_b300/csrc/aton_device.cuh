@@ -342,7 +342,8 @@ __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float
   return o;
 }
 
-// Kahan-compensated FP32 accumulator (per-thread tallies before the FP64 block reduction).
+// Kahan-compensated FP32 accumulator (per-thread tallies of the step kernels before the FP64
+// block reduction; its few extra registers matter there).
 struct KahanF {
   float s = 0.f, c = 0.f;
   __device__ __forceinline__ void add(float v) {
@@ -352,6 +353,21 @@ struct KahanF {
     s = t;
   }
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// Compensated FP32 accumulator for the reduction passes: every addition is split exactly into
+// its rounded sum and rounding error (Knuth's TwoSum, valid whatever the magnitudes, where
+// Kahan's form loses accuracy once a term exceeds the running sum, as photon densities
+// spanning many decades make common), the errors gathered in c; value = s + c.
+struct TwoSumF {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float t = s + v;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (v - bp);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
 }  // namespace aton

@@ -614,12 +614,21 @@ cudaError_t launch_reduce_slots(const Slots& sl, double* out_acc3, unsigned long
 }
 
 // Sum of a float field in FP64, fixed order: per-block partials then one block.
+// Sum of a float field (the stored photons): each thread sums its float4 groups (grid-stride,
+// fixed grid) in a compensated FP32 accumulator (error-free TwoSum) whose value s + c is taken
+// in FP64, then the CTA reduces in FP64. FP32 arithmetic keeps the pass at memory speed (an FP64 add per element
+// is throughput-bound on this part); the compensation keeps the per-thread sums to FP64 quality.
 __global__ void __launch_bounds__(256) k_sum_partial(const float* f, long long n, double* part) {
   __shared__ double s[256];
-  double a = 0;
-  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
-    a += (double)f[i];
-  s[threadIdx.x] = a;
+  TwoSumF k;
+  const long long n4 = n >> 2;
+  const float4* f4 = reinterpret_cast<const float4*>(f);   // cudaMalloc'd: 16-byte aligned
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n4; i += (long long)gridDim.x * 256) {
+    const float4 v = __ldg(f4 + i);
+    k.add(v.x); k.add(v.y); k.add(v.z); k.add(v.w);
+  }
+  if (blockIdx.x == 0 && threadIdx.x < (n & 3)) k.add(f[(n4 << 2) + threadIdx.x]);
+  s[threadIdx.x] = k.value();
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
     if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];

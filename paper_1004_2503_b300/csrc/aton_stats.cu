@@ -5,7 +5,8 @@
 // One pass over N, y, T, nH with a fixed grid, so every sum has a fixed order:
 //  - histogram counts in shared-memory integer atomics, added to global 64-bit counters per CTA
 //    (integer sums: exact in any order);
-//  - the scalar sums in per-thread compensated FP32 accumulators, reduced in FP64 per CTA into a
+//  - the scalar sums in per-thread compensated FP32 accumulators (error-free TwoSum), reduced in
+//    FP64 per CTA into a
 //    per-CTA slot, then summed over the slots in index order;
 //  - the per-density-bin sums of y and N: within each group of 32 consecutive cells (a warp),
 //    runs of equal density bin are summed in FP32 by a segmented tree, and each run's sum is
@@ -32,16 +33,7 @@ __device__ __forceinline__ int find_bin(float v, const float* E, int nb, float g
   return b;
 }
 
-struct Kf {   // compensated FP32 sum
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float v) {
-    const float yv = v - c;
-    const float t = s + yv;
-    c = (t - s) - yv;
-    s = t;
-  }
-  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
-};
+using Kf = TwoSumF;   // compensated FP32 sum
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

@@ -99,10 +99,10 @@ struct Layout {
 
 }  // namespace
 
-// (at TY = 8 the register cap keeps 3 CTAs per SM: 2.81 -> 2.42 ms at 512^3; at TY = 4 the
-// kernel needs no cap, and caps below its 80 registers spill)
+// (no minimum-blocks bound: the compiler's own allocation at TY = 4, 80 registers, is the
+// fastest configuration; any explicit bound changed it, and caps below 80 spill)
 template <int TY, bool PER, bool STD>
-__global__ void __launch_bounds__(kTileX * TY, TY == 8 ? 3 : 1) k_fused_tma(const FusedArgs A,
+__global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
                                                            const __grid_constant__ TmaMaps M) {
   using L = Layout<TY>;
   constexpr int TX = kTileX, NH = 2 * TX + 2 * TY;
