@@ -363,14 +363,18 @@ def ours(args, world, rank, local):
     b.set_fields(pin["N"], pin["Fx"], pin["Fy"], pin["Fz"], pin["T"], pin["nH"], y=ypin)
     b.add_sources(idx, rate)
     b.step(1)
-    b.photon_budget()
+    b.budget_request()
+    b.budget_collect()
     barrier()
     t0 = time.perf_counter()
     b.set_fields(pin["N"], pin["Fx"], pin["Fy"], pin["Fz"], pin["T"], pin["nH"], y=ypin)
-    for _ in range(args.steps):
+    for k in range(args.steps):
         b.add_sources(idx, rate)
         b.step(1)
-        b.photon_budget()
+        if k:
+            b.budget_collect()      # the previous step's budget: ready while this step runs
+        b.budget_request()
+    b.budget_collect()
     b.get_fields(out=outs)
     barrier()
     te = maxtime(time.perf_counter() - t0)
@@ -380,7 +384,8 @@ def ours(args, world, rank, local):
     e2e = {"value": replica_value(world, ncell, args.steps, te), "unit": UNIT,
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
            "what": "set_fields(host, pinned) once + per step add_sources(host) + aton_step(1) "
-                   "+ aton_photon_budget(host) + get_fields(host) once"}
+                   "+ the step's photon budget to the host (aton_budget_request after the step, "
+                   "collected while the next step runs) + get_fields(host) once"}
 
     return finish(args, world, rank, dist, st, idx, rate, run, desc, ncell, value, ms, t,
                   ty, tz, tune_ms, unfused, e2e, launches, clk, rc, diag, bud, kernel)

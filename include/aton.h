@@ -203,6 +203,18 @@ int aton_synchronize(aton_handle h);
  * doubles. Reductions are FP64 and in a fixed order (deterministic). Synchronises. */
 int aton_photon_budget(aton_handle h, double* out);
 
+/* The photon budget without stalling the stream: aton_budget_request queues the reductions of
+ * the budget as of the work queued so far, and a device-to-host copy into the handle's pinned
+ * buffer, and returns at once; aton_budget_collect waits for that copy (only) and returns the
+ * same vector aton_photon_budget would have returned at the request. A driver that requests
+ * after each step and collects the previous request keeps the GPU busy while it reads the
+ * budget of every step. One request is outstanding at a time (a new request replaces one not
+ * collected); collect without a request is STATE.
+ * Errors: STATE (no fields; collect without a request), CUDA (including a pipeline wait that
+ * gave up, reported at collect). */
+int aton_budget_request(aton_handle h);
+int aton_budget_collect(aton_handle h, double* out);
+
 /* Restores a budget saved by aton_photon_budget (checkpoint/restart); the STORED entry is
  * ignored (it is recomputed from the fields). */
 int aton_set_budget(aton_handle h, const double* in);

@@ -35,7 +35,8 @@ EXPORTS = (
     "aton_mlp_get_params", "aton_mlp_fit_norm", "aton_mlp_get_norm", "aton_mlp_set_norm",
     "aton_mlp_features", "aton_mlp_forward", "aton_mlp_loss_grad", "aton_mlp_train_step",
     "aton_mlp_synchronize", "aton_default_stats_params", "aton_ionisation_stats",
-    "aton_equilibrium_neutral_fraction", "aton_star_sources",
+    "aton_equilibrium_neutral_fraction", "aton_star_sources", "aton_budget_request",
+    "aton_budget_collect",
 )
 # layout of aton_star: 7 doubles
 STAR_DTYPE = np.dtype([("x", "<f8"), ("y", "<f8"), ("z", "<f8"), ("mass", "<f8"), ("age", "<f8"),
@@ -126,6 +127,8 @@ def load():
     L.aton_synchronize.argtypes = [_VP]
     L.aton_photon_budget.argtypes = [_VP, C.POINTER(C.c_double)]
     L.aton_set_budget.argtypes = [_VP, C.POINTER(C.c_double)]
+    L.aton_budget_request.argtypes = [_VP]
+    L.aton_budget_collect.argtypes = [_VP, C.POINTER(C.c_double)]
     L.aton_get_diag.argtypes = [_VP, C.POINTER(aton_diag)]
     L.aton_last_error_cells.argtypes = [_VP, C.POINTER(C.c_int64)]
     L.aton_launches_per_step.argtypes = [_VP, C.POINTER(C.c_int)]
@@ -315,6 +318,14 @@ class Aton:
     def photon_budget(self):
         b = (C.c_double * BUDGET_LEN)()
         _check(self.L.aton_photon_budget(self.h, b), "aton_photon_budget")
+        return dict(zip(BUDGET_KEYS, list(b)))
+
+    def budget_request(self):
+        _check(self.L.aton_budget_request(self.h), "aton_budget_request")
+
+    def budget_collect(self):
+        b = (C.c_double * BUDGET_LEN)()
+        _check(self.L.aton_budget_collect(self.h, b), "aton_budget_collect")
         return dict(zip(BUDGET_KEYS, list(b)))
 
     def set_budget(self, budget):

@@ -98,6 +98,14 @@ struct aton_ctx {
   int* sur_list = nullptr;
   int* sur_count = nullptr;
   double quiet_k = 0.0;   // rate bound of the chemistry's cold-gas shortcut (set with prm)
+  // asynchronous budget read: pinned landing area [acc3, stored, timeout word], event, and the
+  // host-side terms as of the request
+  double* bud_pin = nullptr;
+  cudaEvent_t bud_ev = nullptr;
+  bool bud_pending = false;
+  double bud_fold[3] = {0, 0, 0};
+  double bud_emitted = 0, bud_stored0 = 0;
+  double bud_offs[ATON_BUDGET_LEN] = {0};
   // statistics pass
   float* st_edges = nullptr;
   double* st_part = nullptr;
@@ -563,6 +571,8 @@ void aton_finalize(aton_handle h) {
   cudaFree(h->d_src_idx); cudaFree(h->d_src_dN); cudaFree(h->d_tstart); cudaFree(h->d_tsrc);
   cudaFree(h->sur_list); cudaFree(h->sur_count);
   cudaFree(h->st_edges); cudaFree(h->st_part); cudaFree(h->st_out); cudaFree(h->st_u64);
+  if (h->bud_pin) cudaFreeHost(h->bud_pin);
+  if (h->bud_ev) cudaEventDestroy(h->bud_ev);
   if (h->own) cudaStreamDestroy(h->own);
   delete h;
 }
@@ -879,6 +889,59 @@ int aton_photon_budget(aton_handle h, double* out) {
   out[ATON_B_ESCAPED] = acc[1] * h->V + h->offs[ATON_B_ESCAPED];
   out[ATON_B_CLIPPED] = acc[2] * h->V + h->offs[ATON_B_CLIPPED];
   out[ATON_B_STORED0] = h->stored0 + h->offs[ATON_B_STORED0];
+  return ATON_OK;
+}
+
+int aton_budget_request(aton_handle h) {
+  if (int rc = check_h(h)) return rc;
+  if (!h->fields_set) return fail(ATON_ERR_STATE, "aton_set_fields has not been called");
+  if (!h->bud_pin) {
+    CU(cudaMallocHost(&h->bud_pin, sizeof(double) * 5));
+    CU(cudaEventCreateWithFlags(&h->bud_ev, cudaEventDisableTiming));
+  }
+  // a request not collected is replaced: its copy must land before the buffer is reused
+  if (h->bud_pending) CU(cudaEventSynchronize(h->bud_ev));
+  cudaStream_t s = h->stream();
+  if (h->slots.n) {
+    CU(launch_reduce_slots(h->slots, h->d_out, h->d_u64, s));
+  } else {
+    CU(cudaMemsetAsync(h->d_out, 0, sizeof(double) * 3, s));
+  }
+  CU(launch_sum_field(h->f[h->cur][0], h->ncell, h->d_part, h->d_out + 3, s));
+  CU(cudaMemcpyAsync(h->bud_pin, h->d_out, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+  h->bud_pin[4] = 0.0;
+  if (h->slots.timeout) {
+    CU(cudaMemcpyAsync(reinterpret_cast<unsigned int*>(h->bud_pin + 4), h->slots.timeout,
+                       sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+  }
+  CU(cudaEventRecord(h->bud_ev, s));
+  for (int i = 0; i < 3; ++i) h->bud_fold[i] = h->fold_acc[i];
+  h->bud_emitted = h->emitted;
+  h->bud_stored0 = h->stored0;
+  std::memcpy(h->bud_offs, h->offs, sizeof(h->offs));
+  h->bud_pending = true;
+  return ATON_OK;
+}
+
+int aton_budget_collect(aton_handle h, double* out) {
+  if (int rc = check_h(h)) return rc;
+  if (!out) return fail(ATON_ERR_BADARG, "out is NULL");
+  if (!h->bud_pending) return fail(ATON_ERR_STATE, "no budget request is outstanding");
+  h->bud_pending = false;
+  CU(cudaEventSynchronize(h->bud_ev));
+  unsigned int tmo = 0;
+  std::memcpy(&tmo, h->bud_pin + 4, sizeof(tmo));
+  if (tmo) {
+    h->latched = ATON_ERR_CUDA;
+    return fail(ATON_ERR_CUDA, "%u CTAs gave up waiting on a pipeline barrier", tmo);
+  }
+  const double* a = h->bud_pin;
+  out[ATON_B_EMITTED] = h->bud_emitted + h->bud_offs[ATON_B_EMITTED];
+  out[ATON_B_STORED] = a[3] * h->V;
+  out[ATON_B_ABSORBED] = (h->bud_fold[0] + a[0]) * h->V + h->bud_offs[ATON_B_ABSORBED];
+  out[ATON_B_ESCAPED] = (h->bud_fold[1] + a[1]) * h->V + h->bud_offs[ATON_B_ESCAPED];
+  out[ATON_B_CLIPPED] = (h->bud_fold[2] + a[2]) * h->V + h->bud_offs[ATON_B_CLIPPED];
+  out[ATON_B_STORED0] = h->bud_stored0 + h->bud_offs[ATON_B_STORED0];
   return ATON_OK;
 }
 

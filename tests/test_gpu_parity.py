@@ -391,3 +391,33 @@ def test_largest_reduced_flux_is_reported(mode):
     fg = np.sqrt(sum(g[k].astype(np.float64) ** 2 for k in ("Fx", "Fy", "Fz"))) / (c * Ng)
     assert d["max_f"] == pytest.approx(fg[Ng > 1e-30].max(), rel=1e-5)
     assert d["max_f"] <= 1.0 + 1e-6
+
+
+def test_budget_request_and_collect_match_the_synchronous_budget():
+    """aton_budget_request/collect return, without stalling the stream, the budget as of the
+    request: here each step's budget, collected while the next step runs."""
+    st, idx, rate, run = W.workload_small(shape=(12, 16, 20), nsrc=3)
+    a = A.from_workload(st, idx, rate, run)
+    ref = A.from_workload(st, idx, rate, run)
+    with pytest.raises(A.AtonError):
+        a.budget_collect()                     # nothing requested
+    got, want = [], []
+    for k in range(6):
+        a.step(1)
+        if k:
+            got.append(a.budget_collect())
+        a.budget_request()
+        ref.step(1)
+        want.append(ref.photon_budget())
+    got.append(a.budget_collect())
+    a.budget_request()
+    a.budget_request()                         # replaces the one not collected
+    last = a.budget_collect()
+    now = a.photon_budget()
+    a.close()
+    ref.close()
+    for g, w in zip(got, want):
+        for key in g:
+            assert g[key] == pytest.approx(w[key], rel=1e-12, abs=1e-300), key
+    for key in last:
+        assert last[key] == pytest.approx(now[key], rel=1e-12, abs=1e-300), key
