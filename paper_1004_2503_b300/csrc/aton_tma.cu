@@ -12,7 +12,8 @@
 // three-plane ring of vector records per slot, (N, F/c), (Dxx, Dxy, Dxz, Dyy) N and
 // (Dyz, Dzz) N, patching the slots that lie outside the grid from global memory (boundary
 // map; edge tiles only) and computing N D once per slot; a neighbour then costs two or three
-// vector loads. The cell update is the same as in k_fused.
+// vector loads, the z neighbours included (planes z-1, z, z+1 are all in the ring while plane z
+// is updated). The cell update is the same as in k_fused.
 //
 // Used when nx is a multiple of 4 (the tensor-map row pitch must be a multiple of 16 bytes);
 // otherwise the step falls back to k_fused.
@@ -194,18 +195,14 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
     return ring_put(RU + r * L::PLR, RA + r * L::PLR, RB + r * L::PLR, rslot, u);
   };
 
-  float4 um, pm, uc, pc;
-  // plane z0-1: the own column's state and z flux only
+  // plane z0-1 (own slot only) into ring plane 0, plane z0 into ring plane 1
   wait(0);
-  um = prep(stage0, oslot, own_out, ocol, plane_of(z0 - 1));
-  pm = z_flux(um);
-  // plane z0 into ring plane 1
+  put(0, orslot, prep(stage0, oslot, own_out, ocol, plane_of(z0 - 1)));
   {
     wait(1);
     const float* st = stage0 + (1 % kStages) * L::STAGE;
     const int p = plane_of(z0);
-    uc = prep(st, oslot, own_out, ocol, p);
-    pc = put(1, orslot, uc);
+    put(1, orslot, prep(st, oslot, own_out, ocol, p));
     if (hslot >= 0) put(1, hrslot, prep(st, hslot, halo_out, hcol, p));
   }
   int sp = A.tsrc_start[tile];
@@ -215,7 +212,7 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
   long long o = (long long)z0 * plane + ocol;
   float cy = 0.f, cT = 1.f, cn = 1.f;
   if (act) { cy = A.y[o]; cT = A.T[o]; cn = __ldg(A.nH + o); }
-  int rk = 1, rkn = 2;                  // ring planes of z and z+1 (plane index mod 3)
+  int rkm = 0, rk = 1, rkn = 2;         // ring planes of z-1, z and z+1 (plane index mod 3)
   // stages of z and z+1 (plane index mod kStages) and the phase parity of the latter
   int skn = 2 % kStages;
   unsigned pkn = (2 / kStages) & 1;
@@ -242,7 +239,11 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
       while (issued < nplanes && issued <= k + 1 + kStages) issue(issued++);
     }
     if (act) {
-      const int c0 = rk * L::PLR + orslot;
+      const int c0 = rk * L::PLR + orslot, cm = rkm * L::PLR + orslot;
+      const float4 uc = RU[c0], um = RU[cm];
+      const float4 am = RA[cm];
+      const float2 bm = RB[cm];
+      const float4 pm = make_float4(um.w, am.z, bm.x, bm.y);
       float4 u = lf_update(RU + c0, RA + c0, RB + c0, uc, um, pm, up, pp, cu, hl);
       if (!PER) {
         float e = 0.f;
@@ -262,8 +263,8 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
       }
       chem_tally_store<STD>(P, tl, cn, u, cy, cT, A.out, A.y, A.T, o);
     }
-    um = uc; pm = pc; uc = up; pc = pp;
     cy = ny_; cT = nT_; cn = nn_;
+    rkm = rk;
     rk = rkn;
     rkn = rkn == 2 ? 0 : rkn + 1;
     if (++skn == kStages) { skn = 0; pkn ^= 1u; }
