@@ -226,6 +226,38 @@ __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float
   float Nc = N, Tc = T, yc = fminf(fmaxf(y, 0.f), 1.f);
   float Nh = N, Nl = 0.f;   // N as an unevaluated pair Nh + Nl
   ChemOut o{0, 0};
+  // One-sub-step shortcut: cold gas (T_floor to kTExcMin, no collisional terms) whose
+  // recombinations and cooling over the whole step stay below 2^-26 relatively (the quiet test
+  // of the loop below with the whole step), with photo-ionisation Gam dt <= 2^-26 and neither
+  // sub-step limit binding. The loop would take one sub-step h = dt with a = b = 0, and its
+  // Newton change d <= kN y <= 2^-26 y is under half an ulp of y, so y' = y: what is left is
+  // the absorption N' = N / (1 + m y) (m = nH c sigma dt) and the photo-heating of the
+  // temperature update: the loop's own update, up to the rounding of the last operations.
+  {
+    const float xi = 1.f - yc, dt = P.dt;
+    constexpr float kHalfUlp = 1.4901161e-8f;   // 2^-26
+    const float Gam = ksig * Nc;
+    const float gy = Gam * yc * dt;
+    if (Tc < kTExcMin && Tc >= P.T_floor && dt * CRn * xi * xi * P.quiet_k <= kHalfUlp * yc &&
+        Gam * dt <= kHalfUlp && gy <= P.sub_eps * fmaxf(yc, P.y_floor) &&
+        (fixedT || gy * P.eheat_K <= P.sub_eps * Tc * (1.5f * (1.f + xi)))) {
+      const float mY = n * (ksig * dt) * yc;
+      const float r = div_fast(mY, 1.f + mY);   // 1 + mY >= 1
+      const float dN = Nc * r;
+      const float Nn = fmaxf(r > 0.5f ? div_fast(Nc, 1.f + mY) : Nc - dN, 0.f);
+      if (!fixedT)
+        T = fmaxf(div_fast(1.5f * (1.f + xi) * Tc + div_fast(dN, n) * P.eheat_K,
+                           1.5f * (2.f - yc)),
+                  P.T_floor);
+      const float fr = N0 > 0.f ? div_fast(Nn, N0) : 1.f;
+      N = Nn;
+      fx *= fr;
+      fy *= fr;
+      fz *= fr;
+      y = yc;
+      return ChemOut{1, 0};
+    }
+  }
   while (rh > 0.f) {
     if (o.nsub >= P.max_sub) {
       o.err = 1;
@@ -233,11 +265,12 @@ __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float
     }
     const float rem = rh;
     const float xi = 1.f - yc;
-    // Cold gas (below kTExcMin, where the collisional terms are exactly 0 in FP32) whose
+    // Cold gas (T_floor to kTExcMin, where the collisional terms are exactly 0 in FP32) whose
     // recombinations and cooling over the rest of the step would change y and T by less than
     // 2^-26 relatively: those rates are not evaluated, their terms are below half an ulp of
     // the float result (quiet_k bounds alpha_B(T) and (rec(T) + ff(T)) / (1.5 T) there).
-    const bool quiet = Tc < kTExcMin && rem * CRn * xi * xi * P.quiet_k <= 1.4901161e-8f * yc;
+    const bool quiet = Tc < kTExcMin && Tc >= P.T_floor &&
+                       rem * CRn * xi * xi * P.quiet_k <= 1.4901161e-8f * yc;
     float l2T = 0.f, rT = 0.f, l = 0.f, an = 0.f, bn = 0.f;
     if (!quiet) {
       l2T = log2f(Tc);

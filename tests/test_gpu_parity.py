@@ -269,6 +269,14 @@ def test_chemistry_of_single_cells_matches_the_oracle():
         y = 10 ** rng.uniform(-7, 0) if rng.random() < 0.5 else 1 - 10 ** rng.uniform(-6, 0)
         T = 10 ** rng.uniform(0, 6)
         cases.append((N, 0.3 * run["c"] * N, y, T, n))
+    # chemically inert cells (cold, a faint field: the whole-step shortcut) and gas colder than
+    # the floor (T_floor = 1 K), which the shortcuts leave to the full sub-step loop
+    for _ in range(60):
+        n = 10 ** rng.uniform(-9, 1)
+        N = n * 10 ** rng.uniform(-16, -8)
+        y = 1 - 10 ** rng.uniform(-6, -2)
+        T = 10 ** rng.uniform(-2, 3.1)
+        cases.append((N, 0.3 * run["c"] * N, y, T, n))
     worst = dict(x=0.0, T=0.0, N=0.0)
     for N, Fx, y, T, n in cases:
         N32, y32, T32, n32 = (float(np.float32(v)) for v in (N, y, T, n))
