@@ -207,9 +207,12 @@ struct ChemOut {
 // STD selects the standard configuration at compile time (evolving temperature with cooling
 // and collisional ionisation, no clumping), so its flag tests and clumping factors fold away;
 // the kernels take it when the step's parameters are that configuration.
+// F (any units) decays with N; fs is an extra factor applied with that ratio (a unit change the
+// caller wants on the way out, e.g. c to turn F / c back into F).
 template <bool STD = false>
 __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float& N, float& fx,
-                                             float& fy, float& fz, float& y, float& T) {
+                                             float& fy, float& fz, float& y, float& T,
+                                             float fs = 1.f) {
   const bool fixedT = STD ? false : P.fixed_T != 0;
   const bool cool = STD ? true : P.cooling != 0;
   const bool coll = STD ? true : P.coll_ion != 0;
@@ -249,7 +252,7 @@ __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float
         T = fmaxf(div_fast(1.5f * (1.f + xi) * Tc + div_fast(dN, n) * P.eheat_K,
                            1.5f * (2.f - yc)),
                   P.T_floor);
-      const float fr = N0 > 0.f ? div_fast(Nn, N0) : 1.f;
+      const float fr = (N0 > 0.f ? div_fast(Nn, N0) : 1.f) * fs;
       N = Nn;
       fx *= fr;
       fy *= fr;
@@ -365,7 +368,7 @@ __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float
   }
   // F decays by the same factor as N in every sub-step, so by N_final / N_0 overall (after the
   // realisability clamp N = 0 implies F = 0)
-  const float fr = N0 > 0.f ? div_fast(Nc, N0) : 1.f;
+  const float fr = (N0 > 0.f ? div_fast(Nc, N0) : 1.f) * fs;
   N = Nc;
   fx *= fr;
   fy *= fr;

@@ -132,22 +132,22 @@ __device__ __forceinline__ float4 lf_update(const float4* U, const float4* Q, co
                      cu * uc.w - hl * sZ);
 }
 
-// Chemistry of the transported cell, its tallies and the store of the new state (physical F).
+// Chemistry of the transported cell, its tallies and the store of the new state (physical F:
+// the chemistry scales F / c by its photon ratio times c).
 template <bool STD>
 __device__ __forceinline__ void chem_tally_store(const StepParams& P, Tally& tl, float cn, float4 u,
                                                  float cy, float cT, const Fields& out, float* Yf,
                                                  float* Tf, long long o) {
   float Nn = u.x, Xn = u.y, Yn = u.z, Zn = u.w;
   const float N0 = Nn;
-  const ChemOut co = chem_cell<STD>(P, cn, Nn, Xn, Yn, Zn, cy, cT);
+  const ChemOut co = chem_cell<STD>(P, cn, Nn, Xn, Yn, Zn, cy, cT, P.c);
   tl.absorbed.add(N0 - Nn);
   tl.sub += co.nsub;
   tl.mx = max(tl.mx, (unsigned)co.nsub);
   tl.err += co.err;
   // one test: a NaN or an infinity in any of them makes the sum non-finite
   if (!isfinite(Nn + cT + (Xn + Yn + Zn))) tl.nan += 1;
-  const float cl = P.c;
-  out.N[o] = Nn; out.Fx[o] = Xn * cl; out.Fy[o] = Yn * cl; out.Fz[o] = Zn * cl;
+  out.N[o] = Nn; out.Fx[o] = Xn; out.Fy[o] = Yn; out.Fz[o] = Zn;
   Yf[o] = cy; Tf[o] = cT;
 }
 

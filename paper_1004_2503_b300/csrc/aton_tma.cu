@@ -102,7 +102,9 @@ struct Layout {
 
 // (no minimum-blocks bound: the compiler's own allocation at TY = 4, 80 registers, is the
 // fastest configuration; any explicit bound changed it, and caps below 80 spill)
-template <int TY, bool PER, bool STD>
+// FULL: every tile lies inside the grid (nx a multiple of 32, ny of TY), so every thread owns a
+// cell and no own slot needs patching; the bounds tests fold away.
+template <int TY, bool PER, bool STD, bool FULL>
 __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
                                                            const __grid_constant__ TmaMaps M) {
   using L = Layout<TY>;
@@ -153,7 +155,7 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
 
   Tally tl;
   const int gx = x0 + tx, gy = y0 + ty;
-  const bool act = gx < nx && gy < ny;
+  const bool act = FULL || (gx < nx && gy < ny);
   const int oslot = (ty + 1) * kBoxX + (tx + 4);       // stage slot
   const int orslot = (ty + 1) * L::RX + (tx + 1);      // ring slot
   // halo slot of this thread (if any) in tile coordinates
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
     hslot = (hy + 1) * kBoxX + (hx + 4);
     hrslot = (hy + 1) * L::RX + (hx + 1);
   }
-  const bool own_out = !act;
+  const bool own_out = !act;   // (false when FULL)
   const bool halo_out = hslot >= 0 && (x0 + hx < 0 || x0 + hx >= nx || y0 + hy < 0 || y0 + hy >= ny);
   const long long ocol = bc_map(gx, nx, PER) + (long long)nx * bc_map(gy, ny, PER);
   const long long hcol = hslot >= 0 ? bc_map(x0 + hx, nx, PER) + (long long)nx * bc_map(y0 + hy, ny, PER) : 0;
@@ -282,11 +284,14 @@ namespace {
 
 template <int TY, bool PER>
 cudaError_t set_tma_attr() {
-  cudaError_t e = cudaFuncSetAttribute(k_fused_tma<TY, PER, false>,
+  cudaError_t e = cudaFuncSetAttribute(k_fused_tma<TY, PER, false, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)Layout<TY>::BYTES);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_fused_tma<TY, PER, true>,
+  e = cudaFuncSetAttribute(k_fused_tma<TY, PER, true, false>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Layout<TY>::BYTES);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_fused_tma<TY, PER, true, true>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Layout<TY>::BYTES);
 }
 
@@ -294,8 +299,13 @@ template <int TY, bool PER>
 cudaError_t launch_tma_t(const FusedArgs& a, const TmaMaps& m, cudaStream_t s) {
   dim3 grid((a.P.nx + kTileX - 1) / kTileX, (a.P.ny + TY - 1) / TY, (a.P.nz + a.tz - 1) / a.tz);
   dim3 block(kTileX, TY);
-  if (standard_chemistry(a.P)) k_fused_tma<TY, PER, true><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);
-  else k_fused_tma<TY, PER, false><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);
+  const bool full = a.P.nx % kTileX == 0 && a.P.ny % TY == 0;
+  if (!standard_chemistry(a.P))
+    k_fused_tma<TY, PER, false, false><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);
+  else if (full)
+    k_fused_tma<TY, PER, true, true><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);
+  else
+    k_fused_tma<TY, PER, true, false><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);
   return cudaGetLastError();
 }
 
