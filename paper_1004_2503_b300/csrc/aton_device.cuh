@@ -85,6 +85,29 @@ __device__ __forceinline__ ND6 m1_pressure(float N, float fx, float fy, float fz
   return r;
 }
 
+// The same closure as the pair (iso, w) with N D = iso I + w Fh (x) Fh: iso = N (1 - chi)/2 and
+// w = c2 / N (c2 as above; divided by f^2 where |Fh| > N, since D then takes g = Fh / |Fh|).
+// The fused kernels keep this pair per cell (two floats instead of six) and form the components
+// they need from it. w stays normal for N below ~6e37 (c2 >= 3/4).
+__device__ __forceinline__ float2 m1_iso_w(float N, float fx, float fy, float fz) {
+  if (N > kNTiny) {
+    const float rN = rcp_fast(N);   // N in (1e-30, 8e37): the reciprocal stays normal
+    const float gx = fx * rN, gy = fy * rN, gz = fz * rN;
+    float f2 = gx * gx + gy * gy + gz * gz;
+    float k = rN;
+    if (f2 > 1.f) {
+      k = rN * rcp_fast(f2);        // f2 in (1, 3e38]: a normal reciprocal
+      f2 = 1.f;
+    }
+    const float s = sqrtf(4.f - 3.f * f2);        // in [1, 2]
+    const float r5 = rcp_fast(5.f + 2.f * s);
+    const float iso = (1.f + s - 2.f * f2) * (r5 * N);
+    const float w = fmaf(3.f, rcp_fast(2.f + s), 6.f) * r5 * k;
+    return make_float2(iso, w);
+  }
+  return make_float2(N > 0.f ? N * (1.f / 3.f) : 0.f, 0.f);
+}
+
 // ---------------------------------------------------------------------------------------
 // Extreme characteristic speeds (units of c) of the M1 flux Jacobian along an axis, the wave-
 // speed bounds of the HLL flux (section 2.2). With f = |Fh|/N, mu the cosine between Fh and the

@@ -29,11 +29,10 @@ template <int TY, bool PER, bool STD>
 __global__ void __launch_bounds__(kTileX * TY) k_fused(const FusedArgs A) {
   constexpr int TX = kTileX, RX = kRingRX, PLR = RX * (TY + 2);
   constexpr int NH = 2 * TX + 2 * TY;
-  // three-plane ring: [3][PLR] (N, F/c), [3][PLR] N (Dxx, Dxy, Dxz, Dyy), [3][PLR] N (Dyz, Dzz)
+  // three-plane ring: [3][PLR] (N, F/c), [3][PLR] closure pairs (iso, w)
   extern __shared__ float4 ring[];
   float4* RU = ring;
-  float4* RA = RU + 3 * PLR;
-  float2* RB = reinterpret_cast<float2*>(RA + 3 * PLR);
+  float2* RW = reinterpret_cast<float2*>(RU + 3 * PLR);
   const StepParams& P = A.P;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
   const int nx = P.nx, ny = P.ny, nz = P.nz;
@@ -70,8 +69,8 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused(const FusedArgs A) {
   float4 um = ld(pz(z0 - 1) + ocol);
   float4 pm = z_flux(um);
   float4 uc = ld(pz(z0) + ocol);
-  float4 pc = ring_put(RU, RA, RB, oslot, uc);
-  if (hslot >= 0) ring_put(RU, RA, RB, hslot, ld(pz(z0) + hcol));
+  float4 pc = ring_put(RU, RW, oslot, uc);
+  if (hslot >= 0) ring_put(RU, RW, hslot, ld(pz(z0) + hcol));
   float4 nu = ld(pz(z0 + 1) + ocol);
   float4 nh = make_float4(0.f, 0.f, 0.f, 0.f);
   if (hslot >= 0) nh = ld(pz(z0 + 1) + hcol);
@@ -95,8 +94,8 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused(const FusedArgs A) {
     const int rnx = rcur == 2 ? 0 : rcur + 1;
     // plane z+1 into the ring (own and halo slot); its z flux kept in registers
     const float4 up = nu;
-    const float4 pp = ring_put(RU + rnx * PLR, RA + rnx * PLR, RB + rnx * PLR, oslot, up);
-    if (hslot >= 0) ring_put(RU + rnx * PLR, RA + rnx * PLR, RB + rnx * PLR, hslot, nh);
+    const float4 pp = ring_put(RU + rnx * PLR, RW + rnx * PLR, oslot, up);
+    if (hslot >= 0) ring_put(RU + rnx * PLR, RW + rnx * PLR, hslot, nh);
     // prefetch plane z+2 and the chemistry fields of plane z+1
     float ny_ = 0.f, nT_ = 1.f, nn_ = 1.f;
     if (z + 1 < z1) {
@@ -107,7 +106,7 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused(const FusedArgs A) {
     __syncthreads();
     if (act) {
       const int c0 = rcur * PLR + oslot;
-      float4 u = lf_update(RU + c0, RA + c0, RB + c0, uc, um, pm, up, pp, cu, hl);
+      float4 u = lf_update(RU + c0, RW + c0, uc, um, pm, up, pp, cu, hl);
       if (!PER) {  // transmissive faces: outward photon flux through the boundary
         float e = 0.f;
         if (gx == 0) e -= uc.y;
@@ -142,7 +141,7 @@ int fused_tiles(int nx, int ny, int nz, int ty, int tz) {
 
 template <int TY>
 static constexpr size_t fused_smem() {
-  return (size_t)3 * kRingRX * (TY + 2) * (sizeof(float4) * 2 + sizeof(float2));
+  return (size_t)3 * kRingRX * (TY + 2) * (sizeof(float4) + sizeof(float2));
 }
 
 template <int TY, bool PER>

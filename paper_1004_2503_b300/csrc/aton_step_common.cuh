@@ -84,49 +84,57 @@ __device__ __forceinline__ void clamp_state(float& N, float& X, float& Y, float&
 
 // ---------------------------------------------------------------------------------------
 // Cell update shared by the fused kernels. A plane of the three-plane ring holds, per slot
-// (row pitch kTileX + 2, one-cell halo), the records (N, Fx/c, Fy/c, Fz/c), N (Dxx, Dxy, Dxz,
-// Dyy) and N (Dyz, Dzz), so a neighbour costs two or three vector loads.
+// (row pitch kTileX + 2, one-cell halo), the records (N, Fx/c, Fy/c, Fz/c) and the closure pair
+// (iso, w) of m1_iso_w, so a neighbour costs two vector loads and the pressure components a face
+// needs, N D_ij = iso delta_ij + w Fh_i Fh_j, are formed from them. Each product is rounded on
+// its own (no contraction), so a face value is the same number in both cells that use it.
 // ---------------------------------------------------------------------------------------
 constexpr int kRingRX = kTileX + 2;
 
-// Store the record of a slot; returns the cell's z flux (Fz/c, Dxz, Dyz, Dzz) N.
-__device__ __forceinline__ float4 ring_put(float4* RU, float4* RA, float2* RB, int slot,
-                                           const float4& u) {
-  const ND6 d = m1_pressure(u.x, u.y, u.z, u.w);
-  RU[slot] = u;
-  RA[slot] = make_float4(d.xx, d.xy, d.xz, d.yy);
-  RB[slot] = make_float2(d.yz, d.zz);
-  return make_float4(u.w, d.xz, d.yz, d.zz);
+// z flux (Fz/c, Dxz, Dyz, Dzz) N of a state and its closure pair.
+__device__ __forceinline__ float4 z_flux_q(const float4& u, const float2& q) {
+  const float wz = __fmul_rn(q.y, u.w);
+  return make_float4(u.w, __fmul_rn(wz, u.y), __fmul_rn(wz, u.z), fmaf(wz, u.w, q.x));
 }
 
-// z flux (Fz/c, Dxz, Dyz, Dzz) N of a state held in registers.
+// Store the record of a slot; returns the cell's z flux.
+__device__ __forceinline__ float4 ring_put(float4* RU, float2* RW, int slot, const float4& u) {
+  const float2 q = m1_iso_w(u.x, u.y, u.z, u.w);
+  RU[slot] = u;
+  RW[slot] = q;
+  return z_flux_q(u, q);
+}
+
+// z flux of a state held in registers.
 __device__ __forceinline__ float4 z_flux(const float4& u) {
-  const ND6 d = m1_pressure(u.x, u.y, u.z, u.w);
-  return make_float4(u.w, d.xz, d.yz, d.zz);
+  return z_flux_q(u, m1_iso_w(u.x, u.y, u.z, u.w));
 }
 
 // Global Lax-Friedrichs update of the centre cell (section 2.2; Appendix Eqs. A2, A5) from its
-// x and y neighbours in the ring (U, Q, B point at the centre slot) and its z neighbours in
+// x and y neighbours in the ring (U, W point at the centre slot) and its z neighbours in
 // registers (um, pm below; up, pp above): with the face flux (Phi_L + Phi_R)/2 - (u_R - u_L)/2
 // (wave speed c, Fh = F/c units), the update sums, over the six faces, the flux difference
 // minus the neighbour values and is written around the centre value:
 //   u' = (1 - 3 lam) u - lam/2 [sum_d (Phi_d(u_{+d}) - Phi_d(u_{-d})) - sum_nb u_nb].
 // x faces carry (Fx, Dxx, Dxy, Dxz) N, y faces (Fy, Dxy, Dyy, Dyz) N, z faces (Fz, Dxz, Dyz, Dzz) N.
-__device__ __forceinline__ float4 lf_update(const float4* U, const float4* Q, const float2* B,
-                                            const float4& uc, const float4& um, const float4& pm,
-                                            const float4& up, const float4& pp, float cu,
-                                            float hl) {
+__device__ __forceinline__ float4 lf_update(const float4* U, const float2* W, const float4& uc,
+                                            const float4& um, const float4& pm, const float4& up,
+                                            const float4& pp, float cu, float hl) {
   constexpr int RX = kRingRX;
   const float4 uL = U[-1], uR = U[1], uD = U[-RX], uU = U[RX];
-  const float4 aL = Q[-1], aR = Q[1], aD = Q[-RX], aU = Q[RX];
-  const float2 bD = B[-RX], bU = B[RX];
+  const float2 qL = W[-1], qR = W[1], qD = W[-RX], qU = W[RX];
+  const float wL = __fmul_rn(qL.y, uL.y), wR = __fmul_rn(qR.y, uR.y);   // w Fx (x neighbours)
+  const float wD = __fmul_rn(qD.y, uD.z), wU = __fmul_rn(qU.y, uU.z);   // w Fy (y neighbours)
   const float sN = (uR.y - uL.y) + (uU.z - uD.z) + (pp.x - pm.x) -
                    ((uR.x + uL.x) + (uU.x + uD.x) + (up.x + um.x));
-  const float sX = (aR.x - aL.x) + (aU.y - aD.y) + (pp.y - pm.y) -
+  const float sX = (fmaf(wR, uR.y, qR.x) - fmaf(wL, uL.y, qL.x)) +
+                   (__fmul_rn(wU, uU.y) - __fmul_rn(wD, uD.y)) + (pp.y - pm.y) -
                    ((uR.y + uL.y) + (uU.y + uD.y) + (up.y + um.y));
-  const float sY = (aR.y - aL.y) + (aU.w - aD.w) + (pp.z - pm.z) -
+  const float sY = (__fmul_rn(wR, uR.z) - __fmul_rn(wL, uL.z)) +
+                   (fmaf(wU, uU.z, qU.x) - fmaf(wD, uD.z, qD.x)) + (pp.z - pm.z) -
                    ((uR.z + uL.z) + (uU.z + uD.z) + (up.z + um.z));
-  const float sZ = (aR.z - aL.z) + (bU.x - bD.x) + (pp.w - pm.w) -
+  const float sZ = (__fmul_rn(wR, uR.w) - __fmul_rn(wL, uL.w)) +
+                   (__fmul_rn(wU, uU.w) - __fmul_rn(wD, uD.w)) + (pp.w - pm.w) -
                    ((uR.w + uL.w) + (uU.w + uD.w) + (up.w + um.w));
   return make_float4(cu * uc.x - hl * sN, cu * uc.y - hl * sX, cu * uc.z - hl * sY,
                      cu * uc.w - hl * sZ);

@@ -94,7 +94,7 @@ struct Layout {
   static constexpr int PLR = RX * (TY + 2);               // ring slots per plane
   static constexpr unsigned U_BYTES = 4u * PL * 4u;       // bytes landed per plane (u)
   static constexpr size_t STAGE_BYTES = (size_t)kStages * STAGE * 4;
-  static constexpr size_t RING_BYTES = (size_t)3 * PLR * (16 + 16 + 8);
+  static constexpr size_t RING_BYTES = (size_t)3 * PLR * (16 + 8);
   static constexpr size_t BYTES = STAGE_BYTES + RING_BYTES + kStages * 8 + 128;
 };
 
@@ -114,11 +114,10 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
   // access below stays a shared-memory access)
   float* sm = sm_raw + ((128u - (smem_u32(sm_raw) & 127u)) & 127u) / 4;
   float* stage0 = sm;
-  // ring of prepared planes: (N, Fx/c, Fy/c, Fz/c), (Dxx, Dxy, Dxz, Dyy) N, (Dyz, Dzz) N
+  // ring of prepared planes: (N, Fx/c, Fy/c, Fz/c) and the closure pair (iso, w)
   float4* RU = reinterpret_cast<float4*>(sm + kStages * L::STAGE);
-  float4* RA = RU + 3 * L::PLR;
-  float2* RB = reinterpret_cast<float2*>(RA + 3 * L::PLR);
-  unsigned long long* full = reinterpret_cast<unsigned long long*>(RB + 3 * L::PLR);
+  float2* RW = reinterpret_cast<float2*>(RU + 3 * L::PLR);
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(RW + 3 * L::PLR);
 
   const StepParams& P = A.P;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
@@ -194,7 +193,7 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
   };
   // the prepared slot into ring plane r; returns the z flux (Fz/c, Dxz, Dyz, Dzz) N
   auto put = [&](int r, int rslot, const float4& u) {
-    return ring_put(RU + r * L::PLR, RA + r * L::PLR, RB + r * L::PLR, rslot, u);
+    return ring_put(RU + r * L::PLR, RW + r * L::PLR, rslot, u);
   };
 
   // plane z0-1 (own slot only) into ring plane 0, plane z0 into ring plane 1
@@ -243,10 +242,8 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
     if (act) {
       const int c0 = rk * L::PLR + orslot, cm = rkm * L::PLR + orslot;
       const float4 uc = RU[c0], um = RU[cm];
-      const float4 am = RA[cm];
-      const float2 bm = RB[cm];
-      const float4 pm = make_float4(um.w, am.z, bm.x, bm.y);
-      float4 u = lf_update(RU + c0, RA + c0, RB + c0, uc, um, pm, up, pp, cu, hl);
+      const float4 pm = z_flux_q(um, RW[cm]);
+      float4 u = lf_update(RU + c0, RW + c0, uc, um, pm, up, pp, cu, hl);
       if (!PER) {
         float e = 0.f;
         if (gx == 0) e -= uc.y;
