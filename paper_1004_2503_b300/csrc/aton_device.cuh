@@ -291,12 +291,20 @@ __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float
     }
     const float rem = rh;
     const float xi = 1.f - yc;
+    const float Gam = ksig * Nc;
     // Cold gas (T_floor to kTExcMin, where the collisional terms are exactly 0 in FP32) whose
     // recombinations and cooling over the rest of the step would change y and T by less than
     // 2^-26 relatively: those rates are not evaluated, their terms are below half an ulp of
-    // the float result (quiet_k bounds alpha_B(T) and (rec(T) + ff(T)) / (1.5 T) there).
+    // the float result (quiet_k bounds alpha_B(T) and (rec(T) + ff(T)) / (1.5 T) there). The
+    // recombinations enter the implicit update at the end state, whose ionised fraction the
+    // photo-ionisations may raise to at most xm = x + min(Gam rem, 1) y (and y' >= (1 - that) y),
+    // so the test takes xm: the dropped term a xm^2 stays under 2^-26 y'. (Cooling enters at the
+    // start state x.)
+    const float gr = fminf(Gam * rem, 1.f);
+    const float xm = fmaf(gr, yc, xi);
     const bool quiet = Tc < kTExcMin && Tc >= P.T_floor &&
-                       rem * CRn * xi * xi * P.quiet_k <= 1.4901161e-8f * yc;
+                       rem * CRn * xm * xm * P.quiet_k <=
+                           1.4901161e-8f * yc * (1.f - gr);
     float l2T = 0.f, rT = 0.f, l = 0.f, an = 0.f, bn = 0.f;
     if (!quiet) {
       l2T = log2f(Tc);
@@ -306,7 +314,6 @@ __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float
       // the collisional rate is exactly 0 in FP32 below kTBetaMin, so it is not evaluated there
       bn = (coll && Tc > kTBetaMin) ? n * beta_coll(l, l2T, rT) : 0.f;
     }
-    const float Gam = ksig * Nc;
     const float dydt = an * xi * xi - (Gam + bn * xi) * yc;
     float h = rem;
     const float ymax = fmaxf(yc, P.y_floor);

@@ -3,6 +3,8 @@
 Gates (after 100 steps): |x_gpu - x_oracle| <= 1e-3; |T_gpu/T_oracle - 1| <= 1e-3;
 |N_gpu/N_oracle - 1| <= 1e-3 on cells with N > 1e-6 max N. The photon budget closes to 1e-6.
 """
+import itertools
+
 import numpy as np
 import pytest
 
@@ -429,3 +431,32 @@ def test_budget_request_and_collect_match_the_synchronous_budget():
             assert g[key] == pytest.approx(w[key], rel=1e-12, abs=1e-300), key
     for key in last:
         assert last[key] == pytest.approx(now[key], rel=1e-12, abs=1e-300), key
+
+
+def test_weakly_photo_ionised_cold_gas_matches_the_oracle():
+    """Cold, nearly neutral gas (x = 1e-4, 100 K) under photo-ionisation rates from faint to
+    30 per cent per step (Gam dt): a step may raise x by orders of magnitude, so the
+    recombinations at the end of a sub-step can matter where those at its start are negligible. The GPU step
+    must follow the oracle's implicit update to FP32 accuracy here (no shortcut may drop a term
+    that the end state makes visible)."""
+    import oracle as O
+    from parity_helpers import oracle_params
+    st, idx, rate, run = W.workload_small(shape=(2, 2, 2), nsrc=1)
+    ksig_dt = run["c"] * run["sigma_n"] * run["dt"]
+    worst = 0.0
+    # with the temperature fixed no heating limit shortens the sub-step, so one sub-step can
+    # take x from 1e-4 to a few per cent
+    for fixed_T, n, gdt in itertools.product((0, 1), 10.0 ** np.arange(-4.0, 1.01, 0.25),
+                                         (1e-9, 1e-6, 1e-4, 1e-3, 1e-2, 5e-2, 0.1, 0.3)):
+        p = oracle_params(run, fixed_T=fixed_T)
+        N32, y32, T32, n32 = (float(np.float32(v)) for v in (gdt / ksig_dt, 1 - 1e-4, 100.0, n))
+        rc, g, d = _one_cell(run, N32, (0.0, 0.0, 0.0), y32, T32, n32, fixed_T=fixed_T)
+        assert rc == 0
+        r = O.chem_cell(p, n32, N32, [0, 0, 0], 1 - y32, T32)
+        # x = 1 - y is resolved to ~6e-8 near x = 0 in FP32 (two ulps of y allowed)
+        dx = r["x"] - (1 - y32)
+        err = abs(g["x"] - r["x"])
+        worst = max(worst, err / max(dx, 1e-12))
+        assert err <= 1e-4 * dx + 1.2e-7, (fixed_T, n, gdt, g["x"], r["x"], dx)
+        assert abs(g["T"] - r["T"]) <= 1e-5 * r["T"], (fixed_T, n, gdt, g["T"], r["T"])
+    print("weak photo-ionisation worst relative error of the change in x", worst)
