@@ -91,6 +91,15 @@ __device__ __forceinline__ void clamp_state(float& N, float& X, float& Y, float&
 // ---------------------------------------------------------------------------------------
 constexpr int kRingRX = kTileX + 2;
 
+// Paired FP32 arithmetic (one instruction for two lanes on sm_100 and later; each lane rounds
+// like the scalar operation).
+__device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 add2(const float2& a, const float2& b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(const float2& a, const float2& b) {
+  return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+
 // z flux (Fz/c, Dxz, Dyz, Dzz) N of a state and its closure pair.
 __device__ __forceinline__ float4 z_flux_q(const float4& u, const float2& q) {
   const float wz = __fmul_rn(q.y, u.w);
@@ -125,19 +134,24 @@ __device__ __forceinline__ float4 lf_update(const float4* U, const float2* W, co
   const float2 qL = W[-1], qR = W[1], qD = W[-RX], qU = W[RX];
   const float wL = __fmul_rn(qL.y, uL.y), wR = __fmul_rn(qR.y, uR.y);   // w Fx (x neighbours)
   const float wD = __fmul_rn(qD.y, uD.z), wU = __fmul_rn(qU.y, uU.z);   // w Fy (y neighbours)
-  const float sN = (uR.y - uL.y) + (uU.z - uD.z) + (pp.x - pm.x) -
-                   ((uR.x + uL.x) + (uU.x + uD.x) + (up.x + um.x));
-  const float sX = (fmaf(wR, uR.y, qR.x) - fmaf(wL, uL.y, qL.x)) +
-                   (__fmul_rn(wU, uU.y) - __fmul_rn(wD, uD.y)) + (pp.y - pm.y) -
-                   ((uR.y + uL.y) + (uU.y + uD.y) + (up.y + um.y));
-  const float sY = (__fmul_rn(wR, uR.z) - __fmul_rn(wL, uL.z)) +
-                   (fmaf(wU, uU.z, qU.x) - fmaf(wD, uD.z, qD.x)) + (pp.z - pm.z) -
-                   ((uR.z + uL.z) + (uU.z + uD.z) + (up.z + um.z));
-  const float sZ = (__fmul_rn(wR, uR.w) - __fmul_rn(wL, uL.w)) +
-                   (__fmul_rn(wU, uU.w) - __fmul_rn(wD, uD.w)) + (pp.w - pm.w) -
-                   ((uR.w + uL.w) + (uU.w + uD.w) + (up.w + um.w));
-  return make_float4(cu * uc.x - hl * sN, cu * uc.y - hl * sX, cu * uc.z - hl * sY,
-                     cu * uc.w - hl * sZ);
+  // flux differences per component
+  const float fN = (uR.y - uL.y) + (uU.z - uD.z) + (pp.x - pm.x);
+  const float fX = (fmaf(wR, uR.y, qR.x) - fmaf(wL, uL.y, qL.x)) +
+                   (__fmul_rn(wU, uU.y) - __fmul_rn(wD, uD.y)) + (pp.y - pm.y);
+  const float fY = (__fmul_rn(wR, uR.z) - __fmul_rn(wL, uL.z)) +
+                   (fmaf(wU, uU.z, qU.x) - fmaf(wD, uD.z, qD.x)) + (pp.z - pm.z);
+  const float fZ = (__fmul_rn(wR, uR.w) - __fmul_rn(wL, uL.w)) +
+                   (__fmul_rn(wU, uU.w) - __fmul_rn(wD, uD.w)) + (pp.w - pm.w);
+  // the neighbour sums and the update in paired FP32 arithmetic (two components per
+  // instruction, (N, Fx/c) and (Fy/c, Fz/c), the halves of the vector records)
+  const float2 nA = add2(add2(add2(lo2(uR), lo2(uL)), add2(lo2(uU), lo2(uD))),
+                         add2(lo2(up), lo2(um)));
+  const float2 nB = add2(add2(add2(hi2(uR), hi2(uL)), add2(hi2(uU), hi2(uD))),
+                         add2(hi2(up), hi2(um)));
+  const float2 mh = make_float2(-hl, -hl), c2 = make_float2(cu, cu);
+  const float2 rA = __ffma2_rn(mh, sub2(make_float2(fN, fX), nA), __fmul2_rn(c2, lo2(uc)));
+  const float2 rB = __ffma2_rn(mh, sub2(make_float2(fY, fZ), nB), __fmul2_rn(c2, hi2(uc)));
+  return make_float4(rA.x, rA.y, rB.x, rB.y);
 }
 
 // Chemistry of the transported cell, its tallies and the store of the new state (physical F:
