@@ -252,35 +252,52 @@ __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float
   float Nc = N, Tc = T, yc = fminf(fmaxf(y, 0.f), 1.f);
   float Nh = N, Nl = 0.f;   // N as an unevaluated pair Nh + Nl
   ChemOut o{0, 0};
-  // One-sub-step shortcut: cold gas (T_floor to kTExcMin, no collisional terms) whose
-  // recombinations and cooling over the whole step stay below 2^-26 relatively (the quiet test
-  // of the loop below with the whole step), with photo-ionisation Gam dt <= 2^-26 and neither
-  // sub-step limit binding. The loop would take one sub-step h = dt with a = b = 0, and its
-  // Newton change d <= kN y <= 2^-26 y is under half an ulp of y, so y' = y: what is left is
-  // the absorption N' = N / (1 + m y) (m = nH c sigma dt) and the photo-heating of the
-  // temperature update: the loop's own update, up to the rounding of the last operations.
+  // One-sub-step shortcut: the step the loop below takes when its first sub-step is quiet and
+  // spans the whole step: cold gas (T_floor to kTExcMin, no collisional terms) passing the
+  // loop's quiet test with rem = dt, and neither sub-step limit binding. The loop then takes
+  // one sub-step h = dt with a = b = 0, whose balance g = kN y'/(1 + m y') - d = 0 (y' = y - d,
+  // m = nH c sigma dt, kN = c sigma N dt = Gam dt) is the quadratic
+  //   m y'^2 + (1 + kN - m y) y' - y = 0,
+  // solved here in closed form (its root in [0, y], written without cancellation for either
+  // sign of B = 1 + kN - m y), with d taken back from the balance so that it keeps its full
+  // relative precision. Where kN <= 2^-26, d <= kN y is under half an ulp of y and y' = y.
+  // The absorption N' = N / (1 + m y') and the temperature update are the loop's own.
   {
     const float xi = 1.f - yc, dt = P.dt;
     constexpr float kHalfUlp = 1.4901161e-8f;   // 2^-26
-    const float Gam = ksig * Nc;
-    const float gy = Gam * yc * dt;
-    if (Tc < kTExcMin && Tc >= P.T_floor && dt * CRn * xi * xi * P.quiet_k <= kHalfUlp * yc &&
-        Gam * dt <= kHalfUlp && gy <= P.sub_eps * fmaxf(yc, P.y_floor) &&
+    const float kk = ksig * dt;
+    const float kN = kk * Nc;
+    const float gr = fminf(kN, 1.f);
+    const float xm = fmaf(gr, yc, xi);
+    const float gy = kN * yc;
+    if (Tc < kTExcMin && Tc >= P.T_floor &&
+        dt * CRn * xm * xm * P.quiet_k <= kHalfUlp * yc * (1.f - gr) &&
+        gy <= P.sub_eps * fmaxf(yc, P.y_floor) &&
         (fixedT || gy * P.eheat_K <= P.sub_eps * Tc * (1.5f * (1.f + xi)))) {
-      const float mY = n * (ksig * dt) * yc;
+      // (here kN < 1: the quiet test fails at gr = 1)
+      const float m = n * kk;
+      float Y = yc;
+      if (kN > kHalfUlp) {
+        const float B = 1.f + kN - m * yc;
+        const float sD = sqrtf(fmaf(B, B, 4.f * m * yc));
+        // B >= 0: B + sD in [1, 4]; B < 0: m y > 1 + kN, so m > 0
+        const float Yq = B >= 0.f ? div_fast(2.f * yc, B + sD) : div_fast(sD - B, 2.f * m);
+        Y = yc - div_fast(kN * Yq, fmaf(m, Yq, 1.f));
+      }
+      const float mY = m * Y;
       const float r = div_fast(mY, 1.f + mY);   // 1 + mY >= 1
       const float dN = Nc * r;
       const float Nn = fmaxf(r > 0.5f ? div_fast(Nc, 1.f + mY) : Nc - dN, 0.f);
       if (!fixedT)
         T = fmaxf(div_fast(1.5f * (1.f + xi) * Tc + div_fast(dN, n) * P.eheat_K,
-                           1.5f * (2.f - yc)),
+                           1.5f * (2.f - Y)),
                   P.T_floor);
       const float fr = (N0 > 0.f ? div_fast(Nn, N0) : 1.f) * fs;
       N = Nn;
       fx *= fr;
       fy *= fr;
       fz *= fr;
-      y = yc;
+      y = Y;
       return ChemOut{1, 0};
     }
   }
