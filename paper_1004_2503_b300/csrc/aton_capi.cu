@@ -166,6 +166,9 @@ static StepParams step_params(const aton_ctx* h) {
   P.clI_A = (float)h->prm.clump_I_A; P.clI_b = (float)h->prm.clump_I_b;
   P.hll = h->prm.flux == ATON_FLUX_HLL;
   P.quiet_k = (float)h->quiet_k;
+  P.quiet_dt = (float)(h->dt * h->quiet_k * 67108864.0);
+  P.heat_eps = (float)(eheat * kEV / kKBh / (1.5 * h->prm.sub_eps));
+  P.eheat15 = (float)(eheat * kEV / kKBh / 1.5);
   return P;
 }
 

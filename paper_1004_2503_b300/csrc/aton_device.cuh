@@ -25,6 +25,10 @@ struct StepParams {
   float clR_A, clR_b, clI_A, clI_b;
   int hll;             // intercell flux: 0 global Lax-Friedrichs, 1 HLL (plain step only)
   float quiet_k;       // bound of alpha_B(T) and (rec(T) + ff(T)) / (1.5 T), T_floor..kTExcMin
+  // constants of the one-sub-step chemistry shortcut, folded on the host:
+  float quiet_dt;      // dt quiet_k 2^26
+  float heat_eps;      // eheat_K / (1.5 sub_eps)
+  float eheat15;       // eheat_K / 1.5
 };
 
 // ---------------------------------------------------------------------------------------
@@ -270,10 +274,10 @@ __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float
     const float gr = fminf(kN, 1.f);
     const float xm = fmaf(gr, yc, xi);
     const float gy = kN * yc;
-    if (Tc < kTExcMin && Tc >= P.T_floor &&
-        dt * CRn * xm * xm * P.quiet_k <= kHalfUlp * yc * (1.f - gr) &&
+    // (the quiet test and the heating limit with their constants folded on the host)
+    if (Tc < kTExcMin && Tc >= P.T_floor && CRn * P.quiet_dt * xm * xm <= yc * (1.f - gr) &&
         gy <= P.sub_eps * fmaxf(yc, P.y_floor) &&
-        (fixedT || gy * P.eheat_K <= P.sub_eps * Tc * (1.5f * (1.f + xi)))) {
+        (fixedT || gy * P.heat_eps <= Tc * (1.f + xi))) {
       // (here kN < 1: the quiet test fails at gr = 1)
       const float m = n * kk;
       float Y = yc;
@@ -285,14 +289,16 @@ __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float
         Y = yc - div_fast(kN * Yq, fmaf(m, Yq, 1.f));
       }
       const float mY = m * Y;
-      const float r = div_fast(mY, 1.f + mY);   // 1 + mY >= 1
+      const float q = rcp_fast(1.f + mY);   // 1 + mY >= 1
+      const float r = mY * q;
       const float dN = Nc * r;
-      const float Nn = fmaxf(r > 0.5f ? div_fast(Nc, 1.f + mY) : Nc - dN, 0.f);
-      if (!fixedT)
-        T = fmaxf(div_fast(1.5f * (1.f + xi) * Tc + div_fast(dN, n) * P.eheat_K,
-                           1.5f * (2.f - Y)),
+      // N' / N = 1 - r, or 1 / (1 + m y') for a large absorbed fraction
+      const float fN = r > 0.5f ? q : 1.f - r;
+      const float Nn = r > 0.5f ? Nc * q : Nc - dN;
+      if (!fixedT)   // T' = e' / (1.5 (1 + x')): the loop's update with the 1.5 folded
+        T = fmaxf(div_fast(fmaf(div_fast(dN, n), P.eheat15, (1.f + xi) * Tc), 2.f - Y),
                   P.T_floor);
-      const float fr = (N0 > 0.f ? div_fast(Nn, N0) : 1.f) * fs;
+      const float fr = fN * fs;
       N = Nn;
       fx *= fr;
       fy *= fr;
