@@ -33,9 +33,9 @@ HBM_FALLBACK_GBS = 6400.0
 # DRAM bytes per cell-update of the fused kernel from an ncu capture, keyed by the hash of the
 # kernel sources it was taken on (the figure is dropped when the kernel changes).
 NCU_TRAFFIC = {
-    # k_fused_tma, tile 32x4x64, lognormal 256^3: dram__bytes_read.sum 490.30 MB +
-    # dram__bytes_write.sum 362.71 MB per launch over 16,777,216 cells
-    "cc0f7143b7a2": (490.299392e6 + 362.712576e6) / 16777216,
+    # k_fused_tma, tile 32x4x64, lognormal 256^3: dram__bytes_read.sum 489.61 MB +
+    # dram__bytes_write.sum 362.32 MB per launch over 16,777,216 cells
+    "f1d50f24c26f": (489.614592e6 + 362.324480e6) / 16777216,
 }
 
 

@@ -73,14 +73,23 @@ struct aton_ctx {
   int64_t steps = 0;
   int latched = ATON_OK;
   // sources
-  std::map<int64_t, double> src;  // merged: cell -> rate
+  std::vector<std::pair<int64_t, double>> src;  // merged (cell, rate), sorted by cell
+  // pinned staging of the source upload (two buffers, each free again once its event has
+  // completed), so the per-step upload is an asynchronous copy
+  char* src_pin[2] = {nullptr, nullptr};
+  size_t src_pin_cap = 0;
+  cudaEvent_t src_ev[2] = {nullptr, nullptr};
+  int src_pin_i = 0;
   double emit_per_step = 0;       // photons actually injected per step
+  // device copy of the staging layout (one upload per change): the merged list (cell index,
+  // photons per step) and the per-tile records with their tile offsets
+  char* d_srcbuf = nullptr;
+  size_t srcbuf_cap = 0;
   int* d_src_idx = nullptr;
   float* d_src_dN = nullptr;
-  int src_n = 0, src_cap = 0;
+  int src_n = 0;
   int* d_tstart = nullptr;
   TileSrc* d_tsrc = nullptr;
-  int tstart_cap = 0, tsrc_cap = 0;
   bool tiles_dirty = true;
   // execution
   int mode = ATON_MODE_FUSED;
@@ -241,77 +250,91 @@ static int ensure_slots_n(aton_handle h, int need) {
 static int ensure_slots(aton_handle h) { return ensure_slots_n(h, slots_needed(h)); }
 
 // Uploads the merged source list and the per-tile buckets of the current fused tile.
+static size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
 static int upload_sources(aton_handle h) {
   cudaStream_t s = h->stream();
   const int n = (int)h->src.size();
-  std::vector<int> idx(n);
-  std::vector<float> dN(n);
-  double emit = 0;
-  int k = 0;
-  for (auto& kv : h->src) {
-    idx[k] = (int)kv.first;
-    dN[k] = (float)(kv.second * h->dt / h->V);
-    emit += (double)dN[k] * h->V;
-    ++k;
-  }
-  h->emit_per_step = emit;
-  if (n > h->src_cap) {
-    cudaFree(h->d_src_idx); cudaFree(h->d_src_dN);
-    h->d_src_idx = nullptr; h->d_src_dN = nullptr;
-    const int cap = std::max(n, 64);
-    CU(cudaMalloc(&h->d_src_idx, sizeof(int) * cap));
-    CU(cudaMalloc(&h->d_src_dN, sizeof(float) * cap));
-    h->src_cap = cap;
-    drop_graphs(h);
-  }
-  if (n > 0) {
-    CU(cudaMemcpyAsync(h->d_src_idx, idx.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
-    CU(cudaMemcpyAsync(h->d_src_dN, dN.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s));
-  }
-  if (h->src_n != n) drop_graphs(h);  // the unfused source launch size is baked into graphs
-  h->src_n = n;
-  // per-tile buckets sorted by (tile, z)
   const int gxn = (h->nx + kTileX - 1) / kTileX, gyn = (h->ny + h->ty - 1) / h->ty;
   const int ntile = fused_tiles(h->nx, h->ny, h->nz, h->ty, h->tz);
-  std::vector<std::pair<long long, TileSrc>> ent;
-  ent.reserve(n);
-  k = 0;
-  for (auto& kv : h->src) {
-    const int64_t c = kv.first;
+  // staging layout: idx[n] int, dN[n] float, start[ntile+1] int, tile records[n]
+  const size_t o_dN = align16(sizeof(int) * n), o_st = o_dN + align16(sizeof(float) * n);
+  const size_t o_ts = o_st + align16(sizeof(int) * (ntile + 1));
+  const size_t need = o_ts + sizeof(TileSrc) * std::max(n, 1);
+  const int b = h->src_pin_i;
+  for (int q = 0; q < 2; ++q)
+    if (!h->src_ev[q] && cudaEventCreateWithFlags(&h->src_ev[q], cudaEventDisableTiming) != cudaSuccess)
+      return fail(ATON_ERR_CUDA, "cudaEventCreate failed");
+  if (need > h->src_pin_cap) {
+    for (int q = 0; q < 2; ++q) {
+      CU(cudaEventSynchronize(h->src_ev[q]));
+      if (h->src_pin[q]) cudaFreeHost(h->src_pin[q]);
+      h->src_pin[q] = nullptr;
+    }
+    const size_t cap = std::max(need + need / 2, (size_t)65536);
+    for (int q = 0; q < 2; ++q)
+      if (cudaMallocHost(&h->src_pin[q], cap) != cudaSuccess) {
+        h->src_pin_cap = 0;
+        return fail(ATON_ERR_NOMEM, "pinned staging of %zu bytes failed", cap);
+      }
+    h->src_pin_cap = cap;
+  }
+  // the buffer's previous upload has been copied (in practice long ago)
+  CU(cudaEventSynchronize(h->src_ev[b]));
+  char* pb = h->src_pin[b];
+  int* idx = reinterpret_cast<int*>(pb);
+  float* dN = reinterpret_cast<float*>(pb + o_dN);
+  int* start = reinterpret_cast<int*>(pb + o_st);
+  TileSrc* ts = reinterpret_cast<TileSrc*>(pb + o_ts);
+  double emit = 0;
+  for (int k = 0; k < n; ++k) {
+    idx[k] = (int)h->src[k].first;
+    dN[k] = (float)(h->src[k].second * h->dt / h->V);
+    emit += (double)dN[k] * h->V;
+  }
+  h->emit_per_step = emit;
+  if (need > h->srcbuf_cap) {
+    cudaFree(h->d_srcbuf);   // (synchronises: no step still reads it)
+    h->d_srcbuf = nullptr;
+    h->srcbuf_cap = 0;
+    const size_t cap = h->src_pin_cap;
+    CU(cudaMalloc(&h->d_srcbuf, cap));
+    h->srcbuf_cap = cap;
+  }
+  // the kernels' pointers into the buffer move with n and the tile count: captured graphs
+  // hold them (and the unfused source launch size), so they are dropped when these change
+  int* const p_idx = reinterpret_cast<int*>(h->d_srcbuf);
+  float* const p_dN = reinterpret_cast<float*>(h->d_srcbuf + o_dN);
+  int* const p_st = reinterpret_cast<int*>(h->d_srcbuf + o_st);
+  TileSrc* const p_ts = reinterpret_cast<TileSrc*>(h->d_srcbuf + o_ts);
+  if (p_idx != h->d_src_idx || p_dN != h->d_src_dN || p_st != h->d_tstart ||
+      p_ts != h->d_tsrc || h->src_n != n)
+    drop_graphs(h);
+  h->d_src_idx = p_idx; h->d_src_dN = p_dN; h->d_tstart = p_st; h->d_tsrc = p_ts;
+  h->src_n = n;
+  // per-tile records ordered by (tile, z, cell): the merged list is sorted by cell index, so
+  // within a tile it is already in (z, cell) order and a stable counting sort by tile suffices
+  std::vector<int> tile_of(n);
+  std::fill(start, start + ntile + 1, 0);
+  for (int k = 0; k < n; ++k) {
+    const int64_t c = h->src[k].first;
     const int i = (int)(c % h->nx), j = (int)((c / h->nx) % h->ny), z = (int)(c / ((int64_t)h->nx * h->ny));
     const int bx = i / kTileX, by = j / h->ty, bz = z / h->tz;
-    const long long tile = bx + (long long)gxn * (by + (long long)gyn * bz);
-    TileSrc t{z, (i - bx * kTileX) + kTileX * (j - by * h->ty), dN[k], 0};
-    ent.push_back({tile * (long long)h->nz + z, t});
-    ++k;
-  }
-  std::sort(ent.begin(), ent.end(), [](const auto& a, const auto& b) {
-    return a.first < b.first || (a.first == b.first && a.second.cell < b.second.cell);
-  });
-  std::vector<int> start(ntile + 1, 0);
-  std::vector<TileSrc> ts(std::max(n, 1));
-  for (int e = 0; e < n; ++e) {
-    start[ent[e].first / h->nz + 1] += 1;
-    ts[e] = ent[e].second;
+    tile_of[k] = bx + gxn * (by + gyn * bz);
+    start[tile_of[k] + 1] += 1;
   }
   for (int t = 0; t < ntile; ++t) start[t + 1] += start[t];
-  if (ntile + 1 > h->tstart_cap) {
-    cudaFree(h->d_tstart);
-    h->d_tstart = nullptr;
-    CU(cudaMalloc(&h->d_tstart, sizeof(int) * (ntile + 1)));
-    h->tstart_cap = ntile + 1;
-    drop_graphs(h);
+  {
+    std::vector<int> fill(start, start + ntile);
+    for (int k = 0; k < n; ++k) {
+      const int64_t c = h->src[k].first;
+      const int i = (int)(c % h->nx), j = (int)((c / h->nx) % h->ny), z = (int)(c / ((int64_t)h->nx * h->ny));
+      ts[fill[tile_of[k]]++] = TileSrc{z, (i % kTileX) + kTileX * (j % h->ty), dN[k], 0};
+    }
   }
-  if (std::max(n, 1) > h->tsrc_cap) {
-    cudaFree(h->d_tsrc);
-    h->d_tsrc = nullptr;
-    const int cap = std::max(n, 64);
-    CU(cudaMalloc(&h->d_tsrc, sizeof(TileSrc) * cap));
-    h->tsrc_cap = cap;
-    drop_graphs(h);
-  }
-  CU(cudaMemcpyAsync(h->d_tstart, start.data(), sizeof(int) * (ntile + 1), cudaMemcpyHostToDevice, s));
-  if (n > 0) CU(cudaMemcpyAsync(h->d_tsrc, ts.data(), sizeof(TileSrc) * n, cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(h->d_srcbuf, pb, need, cudaMemcpyHostToDevice, s));
+  CU(cudaEventRecord(h->src_ev[b], s));
+  h->src_pin_i = 1 - b;
   h->tiles_dirty = false;
   return ATON_OK;
 }
@@ -571,10 +594,15 @@ void aton_finalize(aton_handle h) {
   cudaFree(h->y); cudaFree(h->T); cudaFree(h->nH);
   cudaFree(h->d_part); cudaFree(h->d_out); cudaFree(h->d_u64); cudaFree(h->d_bad);
   free_slots(h->slots);
-  cudaFree(h->d_src_idx); cudaFree(h->d_src_dN); cudaFree(h->d_tstart); cudaFree(h->d_tsrc);
+  cudaFree(h->d_srcbuf);
   cudaFree(h->sur_list); cudaFree(h->sur_count);
   cudaFree(h->st_edges); cudaFree(h->st_part); cudaFree(h->st_out); cudaFree(h->st_u64);
   if (h->bud_pin) cudaFreeHost(h->bud_pin);
+  for (int b = 0; b < 2; ++b) {
+    if (h->src_ev[b]) cudaEventSynchronize(h->src_ev[b]);
+    if (h->src_pin[b]) cudaFreeHost(h->src_pin[b]);
+    if (h->src_ev[b]) cudaEventDestroy(h->src_ev[b]);
+  }
   if (h->bud_ev) cudaEventDestroy(h->bud_ev);
   if (h->own) cudaStreamDestroy(h->own);
   delete h;
@@ -793,8 +821,19 @@ int aton_add_sources(aton_handle h, const int64_t* cell_idx, const double* rate,
     if (!(rate[i] >= 0) || !std::isfinite(rate[i]))
       return fail(ATON_ERR_BADARG, "source %lld: rate must be finite and >= 0", (long long)i);
   }
-  if (mode == ATON_SRC_REPLACE) h->src.clear();
-  for (int64_t i = 0; i < n; ++i) h->src[cell_idx[i]] += rate[i];
+  // merged list sorted by cell; a cell listed more than once (or already present, when
+  // appending) gets its rates summed in the order given
+  std::vector<std::pair<int64_t, double>> all;
+  all.reserve((mode == ATON_SRC_APPEND ? h->src.size() : 0) + (size_t)n);
+  if (mode == ATON_SRC_APPEND) all = h->src;
+  for (int64_t i = 0; i < n; ++i) all.emplace_back(cell_idx[i], rate[i]);
+  std::stable_sort(all.begin(), all.end(),
+                   [](const auto& a, const auto& b) { return a.first < b.first; });
+  h->src.clear();
+  for (const auto& e : all) {
+    if (!h->src.empty() && h->src.back().first == e.first) h->src.back().second += e.second;
+    else h->src.push_back(e);
+  }
   return upload_sources(h);
 }
 

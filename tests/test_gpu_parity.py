@@ -460,3 +460,26 @@ def test_weakly_photo_ionised_cold_gas_matches_the_oracle():
         assert err <= 1e-4 * dx + 1.2e-7, (fixed_T, n, gdt, g["x"], r["x"], dx)
         assert abs(g["T"] - r["T"]) <= 1e-5 * r["T"], (fixed_T, n, gdt, g["T"], r["T"])
     print("weak photo-ionisation worst relative error of the change in x", worst)
+
+
+def test_source_lists_merge_and_append():
+    """Sources given in pieces (a cell listed twice with half its rate each, the list split
+    between a replacing and an appending call) step exactly like the merged list."""
+    st, idx, rate, run = W.workload_small(shape=(8, 16, 32), nsrc=5, seed_field=41, seed_src=42)
+    ref, bref, _, _ = run_gpu(st, idx, rate, run, 10)
+    a = A.from_workload(st, idx[:0], rate[:0], run)
+    try:
+        half = len(idx) // 2
+        dup_i = np.concatenate([idx[:half], idx[:half]])
+        dup_r = np.concatenate([rate[:half] / 2, rate[:half] / 2])
+        a.add_sources(dup_i, dup_r)                                   # replace
+        a.add_sources(idx[half:][::-1], rate[half:][::-1], mode=A.SRC_APPEND)
+        a.step(10)
+        assert a.synchronize() == 0
+        f = a.get_fields()
+        b = a.photon_budget()
+    finally:
+        a.close()
+    for k in ("N", "Fx", "Fy", "Fz", "y", "T"):
+        assert np.array_equal(f[k], ref[k]), k
+    assert b["emitted"] == pytest.approx(bref["emitted"], rel=1e-12)
