@@ -5,8 +5,9 @@
 //
 // Fused path (one kernel per step): each CTA owns a 32 x TY column tile of the grid and a
 // z-slab of tz planes, and marches through the slab plane by plane. The (N, Fh) plane with a
-// one-cell halo and the M1 pressure N D of each of its cells (computed once per cell) sit in
-// a three-deep shared-memory ring; the z neighbours of the own column stay in registers. For
+// one-cell halo and the M1 closure pair (iso, w) of each of its cells (N D = iso I + w Fh Fh^T,
+// evaluated once per cell) sit in a three-deep shared-memory ring; the z neighbours of the own
+// column stay in registers. For
 // every cell of a plane the kernel then does the Lax-Friedrichs transport (section 2.2;
 // Appendix Eqs. A2, A5), the realisability clamp, the point-source injection (section 2.3)
 // and the chemistry/cooling/absorption operator Phi (Appendix Eq. A4), and stores N, Fh, y,

@@ -9,11 +9,11 @@
 // barrier that ends its use, three planes ahead of the next use, so no thread waits on a free
 // stage and no warp is spent on producing. The chemistry fields y, T, nH of the own cell are
 // loaded one plane ahead into registers. Every thread turns each landed plane into a
-// three-plane ring of vector records per slot, (N, F/c), (Dxx, Dxy, Dxz, Dyy) N and
-// (Dyz, Dzz) N, patching the slots that lie outside the grid from global memory (boundary
-// map; edge tiles only) and computing N D once per slot; a neighbour then costs two or three
-// vector loads, the z neighbours included (planes z-1, z, z+1 are all in the ring while plane z
-// is updated). The cell update is the same as in k_fused.
+// three-plane ring of two vector records per slot, (N, F/c) and the closure pair (iso, w) with
+// N D = iso I + w (F/c)(F/c)^T, patching the slots that lie outside the grid from global memory
+// (boundary map; edge tiles only) and evaluating the closure once per slot; a neighbour then
+// costs two vector loads, the z neighbours included (planes z-1, z, z+1 are all in the ring
+// while plane z is updated). The cell update is the same as in k_fused.
 //
 // Used when nx is a multiple of 4 (the tensor-map row pitch must be a multiple of 16 bytes);
 // otherwise the step falls back to k_fused.
@@ -100,8 +100,8 @@ struct Layout {
 
 }  // namespace
 
-// (no minimum-blocks bound: the compiler's own allocation at TY = 4, 80 registers, is the
-// fastest configuration; any explicit bound changed it, and caps below 80 spill)
+// (no minimum-blocks bound: the compiler's own allocation at TY = 4, 72 registers and seven
+// CTAs per SM, is the fastest configuration; a cap at 64 for eight CTAs spilled and ran slower)
 // FULL: every tile lies inside the grid (nx a multiple of 32, ny of TY), so every thread owns a
 // cell and no own slot needs patching; the bounds tests fold away.
 template <int TY, bool PER, bool STD, bool FULL>
