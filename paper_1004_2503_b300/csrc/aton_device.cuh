@@ -93,23 +93,21 @@ __device__ __forceinline__ ND6 m1_pressure(float N, float fx, float fy, float fz
 // w = c2 / N (c2 as above; divided by f^2 where |Fh| > N, since D then takes g = Fh / |Fh|).
 // The fused kernels keep this pair per cell (two floats instead of six) and form the components
 // they need from it. w stays normal for N below ~6e37 (c2 >= 3/4).
+// Written without branches (the fused kernels evaluate it for every slot of a plane): the
+// closure of an empty cell (N <= kNTiny) is evaluated on a stand-in N = 1 and replaced by the
+// isotropic pair at the end, and the f > 1 rescaling is a selection.
 __device__ __forceinline__ float2 m1_iso_w(float N, float fx, float fy, float fz) {
-  if (N > kNTiny) {
-    const float rN = rcp_fast(N);   // N in (1e-30, 8e37): the reciprocal stays normal
-    const float gx = fx * rN, gy = fy * rN, gz = fz * rN;
-    float f2 = gx * gx + gy * gy + gz * gz;
-    float k = rN;
-    if (f2 > 1.f) {
-      k = rN * rcp_fast(f2);        // f2 in (1, 3e38]: a normal reciprocal
-      f2 = 1.f;
-    }
-    const float s = sqrtf(4.f - 3.f * f2);        // in [1, 2]
-    const float r5 = rcp_fast(5.f + 2.f * s);
-    const float iso = (1.f + s - 2.f * f2) * (r5 * N);
-    const float w = fmaf(3.f, rcp_fast(2.f + s), 6.f) * r5 * k;
-    return make_float2(iso, w);
-  }
-  return make_float2(N > 0.f ? N * (1.f / 3.f) : 0.f, 0.f);
+  const bool rad = N > kNTiny;
+  const float rN = rcp_fast(rad ? N : 1.f);   // N in (1e-30, 8e37): the reciprocal stays normal
+  const float gx = fx * rN, gy = fy * rN, gz = fz * rN;
+  float f2 = gx * gx + gy * gy + gz * gz;
+  const float k = f2 > 1.f ? rN * rcp_fast(f2) : rN;   // f2 in (1, 3e38]: a normal reciprocal
+  f2 = fminf(f2, 1.f);
+  const float s = sqrtf(4.f - 3.f * f2);        // in [1, 2]
+  const float r5 = rcp_fast(5.f + 2.f * s);
+  const float iso = (1.f + s - 2.f * f2) * (r5 * N);
+  const float w = fmaf(3.f, rcp_fast(2.f + s), 6.f) * r5 * k;
+  return rad ? make_float2(iso, w) : make_float2(N > 0.f ? N * (1.f / 3.f) : 0.f, 0.f);
 }
 
 // ---------------------------------------------------------------------------------------
