@@ -34,9 +34,9 @@ HBM_FALLBACK_GBS = 6400.0
 # DRAM bytes per cell-update of the fused kernel from an ncu capture, keyed by the hash of the
 # kernel sources it was taken on (the figure is dropped when the kernel changes).
 NCU_TRAFFIC = {
-    # k_fused_tma, tile 32x4x64, lognormal 256^3: dram__bytes_read.sum 489.61 MB +
-    # dram__bytes_write.sum 362.32 MB per launch over 16,777,216 cells
-    "29271c739091": (489.614592e6 + 362.324480e6) / 16777216,
+    # k_fused_tma, tile 32x4x64, lognormal 256^3: dram__bytes_read.sum 487.49 MB +
+    # dram__bytes_write.sum 363.13 MB per launch over 16,777,216 cells
+    "f4cb6172e03b": (487.488256e6 + 363.130880e6) / 16777216,
 }
 
 
