@@ -20,6 +20,7 @@ import re
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -79,7 +80,9 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{index}.csv")
+        # the raw samples (a CSV kept beside the run: ATON_CLOCKS_DIR, else the temp directory)
+        folder = os.environ.get("ATON_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(folder, f"clocks_bench_{index}.csv")
 
     def start(self):
         try:
