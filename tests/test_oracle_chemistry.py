@@ -193,3 +193,32 @@ def test_gas_at_the_floor_that_would_cool_takes_one_substep():
     r = O.chem_cell(p, 1e-3, 0.0, [0, 0, 0], 1e-4, p.T_floor)
     assert r["err"] == 0 and r["nsub"] == 1
     assert r["T"] == pytest.approx(p.T_floor, rel=1e-6)
+
+
+def test_one_quiet_substep_is_the_quadratic_the_kernels_solve_in_closed_form():
+    """With recombinations and collisional terms negligible (hot, fixed T; a = b = 0), one
+    implicit sub-step y' - y = -c sigma N' y' h with N' = N / (1 + m y') is the quadratic
+    m y'^2 + (1 + kN - m y) y' - y = 0 (m = nH c sigma h, kN = c sigma N h). The oracle's
+    Newton step must land on its root, taken here in the cancellation-free form for either sign
+    of B = 1 + kN - m y, with d = kN y' / (1 + m y') (the form the fused kernels evaluate)."""
+    T = 1e6
+    cases = [(1e-8, 1e10, 0.01), (1e-8, 1e10, 0.5), (1.0, 1e8, 0.05), (1.0, 1e8, 0.5),
+             (3e-3, 1e10, 0.2)]
+    for n, dt, kN in cases:
+        y = 0.9
+        N = kN / (C * SIG * dt)
+        m = n * C * SIG * dt
+        B = 1 + kN - m * y
+        sD = math.sqrt(B * B + 4 * m * y)
+        Yq = 2 * y / (B + sD) if B >= 0 else (sD - B) / (2 * m)
+        d = kN * Yq / (1 + m * Yq)
+        y_cf = y - d
+        r = O.chem_cell(_chem(dt, 1.0), n, N, [0, 0, 0], 1 - y, T)
+        assert r["nsub"] == 1, (n, dt, kN)
+        # the recombinations left out of the quadratic, alpha nH dt x'^2, bound the difference
+        tol = 2 * O.alpha_B(T) * n * dt * (1 - y_cf) ** 2 + 1e-12
+        assert abs((1 - r["x"]) - y_cf) <= tol, (n, dt, kN, 1 - r["x"], y_cf)
+        assert r["N"] == pytest.approx(N / (1 + m * y_cf), rel=1e-9 + 10 * tol)
+        assert (B < 0) == (m * y > 1 + kN)
+    # both signs of B are covered
+    assert any(n * C * SIG * dt * 0.9 > 1 + kN for n, dt, kN in cases)
