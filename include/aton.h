@@ -181,10 +181,13 @@ int aton_get_fields(aton_handle h, float* N, float* Fx, float* Fy, float* Fz, fl
                     float* y, float* T, int where);
 
 /* Sets (REPLACE) or extends (APPEND) the point-source list: cell_idx[s] in [0, ncell) (linear
- * index as above), rate_per_s[s] >= 0 photons/s. Host arrays. Sources in the same cell are
- * summed. Each step adds rate*dt/V to N of its cell after transport and before chemistry
- * (section 2.3 nearest-grid-point emission; S in Eq. 3 and Appendix Eq. A2).
- * Errors: BADARG (index out of range, negative or non-finite rate, n < 0, bad mode). */
+ * index as above), rate_per_s[s] >= 0 photons/s. Host arrays, read before the call returns
+ * (the caller may reuse them at once; the device copy is queued on the handle's stream without
+ * waiting for a running step). Sources in the same cell are summed, in the order given after
+ * any existing entry. Each step adds rate*dt/V to N of its cell after transport and before
+ * chemistry (section 2.3 nearest-grid-point emission; S in Eq. 3 and Appendix Eq. A2).
+ * Errors: BADARG (index out of range, negative or non-finite rate, n < 0, bad mode), NOMEM
+ * (pinned staging), CUDA. */
 int aton_add_sources(aton_handle h, const int64_t* cell_idx, const double* rate_per_s,
                      int64_t n, int mode);
 
