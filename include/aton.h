@@ -96,8 +96,9 @@ typedef struct {
  * normal, lo, hi = c (chi' mu -/+ sqrt((chi' mu)^2 - C)) / 2,
  * C = (1 - mu^2)((3 chi - 1) chi' / f - 2) + 2 chi (1 - 3 mu^2) + 2 chi' f (3 mu^2 - 1)
  * (the roots of the Jacobian's characteristic polynomial besides the transverse speed
- * c (3 chi - 1) mu / (2 f); +-c/sqrt(3) at f = 0, c mu at f = 1). HLL runs through the plain
- * (three-kernel) step whatever the execution mode. */
+ * c (3 chi - 1) mu / (2 f); +-c/sqrt(3) at f = 0, c mu at f = 1). HLL runs in the one-launch
+ * fused step in ATON_MODE_FUSED when nx is a multiple of 4, otherwise through the plain
+ * (three-kernel) step. */
 #define ATON_FLUX_GLF 0
 #define ATON_FLUX_HLL 1
 

@@ -339,14 +339,20 @@ static int upload_sources(aton_handle h) {
   return ATON_OK;
 }
 
+// Steps that take the plain three-kernel path whatever the execution mode: with the pair sink or
+// the surrogate, and with the HLL flux unless the TMA-staged fused kernel can run it.
+static bool plain_only(const aton_ctx* h) {
+  const bool hll_fused = h->mode == ATON_MODE_FUSED && h->tma_ok[ty_index(h->ty)];
+  return h->sink != nullptr || (h->sur && h->sur_p.enabled) ||
+         (h->prm.flux == ATON_FLUX_HLL && !hll_fused);
+}
+
 static int enqueue_step(aton_handle h, cudaStream_t s) {
   const int nxt = 1 - h->cur;
   const Fields in{h->f[h->cur][0], h->f[h->cur][1], h->f[h->cur][2], h->f[h->cur][3]};
   const Fields out{h->f[nxt][0], h->f[nxt][1], h->f[nxt][2], h->f[nxt][3]};
   cudaError_t e;
-  const bool plain_only = h->sink != nullptr || (h->sur && h->sur_p.enabled) ||
-                          h->prm.flux == ATON_FLUX_HLL;
-  if (!plain_only && (h->mode == ATON_MODE_FUSED || h->mode == ATON_MODE_FUSED_LDG)) {
+  if (!plain_only(h) && (h->mode == ATON_MODE_FUSED || h->mode == ATON_MODE_FUSED_LDG)) {
     FusedArgs a{};
     a.P = step_params(h);
     a.in = in; a.out = out;
@@ -1039,8 +1045,7 @@ int aton_launches_per_step(aton_handle h, int* launches) {
   if (!launches) return fail(ATON_ERR_BADARG, "launches is NULL");
   if (h->mode == ATON_MODE_FUSED || h->mode == ATON_MODE_FUSED_LDG) *launches = 1;
   else *launches = h->src_n > 0 ? plain_launches() : plain_launches() - 1;
-  if ((h->sink || (h->sur && h->sur_p.enabled) || h->prm.flux == ATON_FLUX_HLL) &&
-      *launches == 1)
+  if (plain_only(h) && *launches == 1)
     *launches = h->src_n > 0 ? plain_launches() : plain_launches() - 1;
   if (h->sur && h->sur_p.enabled) *launches += 1;   // the candidate pass (plus a counter reset)
   return ATON_OK;

@@ -193,12 +193,6 @@ __device__ __forceinline__ void load_u(const Fields& f, long long o, float rc, f
   u[3] = __ldg(f.Fz + o) * rc;
 }
 
-// HLL face flux of one component: (l+ Phi_L - l- Phi_R + l+ l- (u_R - u_L)) / (l+ - l-)
-__device__ __forceinline__ float hll_face(float lm, float lp, float rd, float PL, float PR,
-                                          float uL, float uR) {
-  return (lp * PL - lm * PR + lp * lm * (uR - uL)) * rd;
-}
-
 template <bool PER, bool HLL>
 __global__ void __launch_bounds__(kPlainThreads) k_plain_transport(const PlainArgs A) {
   const StepParams& P = A.P;

@@ -154,6 +154,83 @@ __device__ __forceinline__ float4 lf_update(const float4* U, const float2* W, co
   return make_float4(rA.x, rA.y, rB.x, rB.y);
 }
 
+// ---------------------------------------------------------------------------------------
+// HLL intercell flux in the fused kernel (section 2.2 offers HLL beside Lax-Friedrichs). Each
+// ring slot also keeps its cell's wave-speed bounds (units of c) along x, y and z: the extreme
+// eigenvalues of the M1 flux Jacobian (m1_speeds, m1_axis_speeds). The face flux is
+//   (l+ Phi_L - l- Phi_R + l+ l- (u_R - u_L)) / (l+ - l-),
+//   l- = min(0, lo_L, lo_R), l+ = max(0, hi_L, hi_R),
+// with the mean of the two fluxes where l+ - l- vanishes (both cells streaming at f = 1
+// parallel to the face, where those fluxes vanish too).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void ring_put_speeds(float2* SX, float2* SY, float2* SZ, int slot,
+                                                const float4& u) {
+  const M1Speeds m = m1_speeds(u.x, u.y, u.z, u.w);
+  float lo, hi;
+  m1_axis_speeds(m, m.gx, lo, hi);
+  SX[slot] = make_float2(lo, hi);
+  m1_axis_speeds(m, m.gy, lo, hi);
+  SY[slot] = make_float2(lo, hi);
+  m1_axis_speeds(m, m.gz, lo, hi);
+  SZ[slot] = make_float2(lo, hi);
+}
+
+// fluxes along x and y of a state and its closure pair (along z: z_flux_q)
+__device__ __forceinline__ float4 x_flux_q(const float4& u, const float2& q) {
+  const float w = __fmul_rn(q.y, u.y);
+  return make_float4(u.y, fmaf(w, u.y, q.x), __fmul_rn(w, u.z), __fmul_rn(w, u.w));
+}
+__device__ __forceinline__ float4 y_flux_q(const float4& u, const float2& q) {
+  const float w = __fmul_rn(q.y, u.z);
+  return make_float4(u.z, __fmul_rn(w, u.y), fmaf(w, u.z, q.x), __fmul_rn(w, u.w));
+}
+
+// HLL face flux of one component: (l+ Phi_L - l- Phi_R + l+ l- (u_R - u_L)) / (l+ - l-)
+__device__ __forceinline__ float hll_face(float lm, float lp, float rd, float PL, float PR,
+                                          float uL, float uR) {
+  return (lp * PL - lm * PR + lp * lm * (uR - uL)) * rd;
+}
+
+// (flux through the high face) - (flux through the low face) along one axis, for the centre c
+// between its low (l) and high (h) neighbours
+__device__ __forceinline__ float4 hll_axis(const float4& fl, const float4& fc, const float4& fh,
+                                           const float4& ul, const float4& uc, const float4& uh,
+                                           const float2& sl, const float2& sc, const float2& sh) {
+  const float lmp = fminf(0.f, fminf(sc.x, sh.x)), lpp = fmaxf(0.f, fmaxf(sc.y, sh.y));
+  const float lmm = fminf(0.f, fminf(sl.x, sc.x)), lpm = fmaxf(0.f, fmaxf(sl.y, sc.y));
+  const float dp = lpp - lmp, dm = lpm - lmm;
+  const bool gp = dp > 1e-6f, gm = dm > 1e-6f;
+  const float rp = rcp_fast(gp ? dp : 1.f), rm = rcp_fast(gm ? dm : 1.f);   // dp, dm <= 2
+  auto face = [&](bool g, float lm, float lp, float rd, float PL, float PR, float uL, float uR) {
+    return g ? hll_face(lm, lp, rd, PL, PR, uL, uR) : 0.5f * (PL + PR);
+  };
+  return make_float4(
+      face(gp, lmp, lpp, rp, fc.x, fh.x, uc.x, uh.x) - face(gm, lmm, lpm, rm, fl.x, fc.x, ul.x, uc.x),
+      face(gp, lmp, lpp, rp, fc.y, fh.y, uc.y, uh.y) - face(gm, lmm, lpm, rm, fl.y, fc.y, ul.y, uc.y),
+      face(gp, lmp, lpp, rp, fc.z, fh.z, uc.z, uh.z) - face(gm, lmm, lpm, rm, fl.z, fc.z, ul.z, uc.z),
+      face(gp, lmp, lpp, rp, fc.w, fh.w, uc.w, uh.w) - face(gm, lmm, lpm, rm, fl.w, fc.w, ul.w, uc.w));
+}
+
+// HLL update of the centre cell: u' = u - lam sum_d (F_{d,+} - F_{d,-}). U, W, SX, SY point at
+// the centre slot of plane z; the z neighbours come as (state, closure pair, z speeds).
+__device__ __forceinline__ float4 hll_update(const float4* U, const float2* W, const float2* SX,
+                                             const float2* SY, const float2* SZ, const float4& uc,
+                                             const float4& um, const float2& qm,
+                                             const float2& szm, const float4& up,
+                                             const float2& qp, const float2& szp, float lam) {
+  constexpr int RX = kRingRX;
+  const float2 qc = W[0];
+  const float4 uL = U[-1], uR = U[1], uD = U[-RX], uU = U[RX];
+  const float4 ax = hll_axis(x_flux_q(uL, W[-1]), x_flux_q(uc, qc), x_flux_q(uR, W[1]), uL, uc,
+                             uR, SX[-1], SX[0], SX[1]);
+  const float4 ay = hll_axis(y_flux_q(uD, W[-RX]), y_flux_q(uc, qc), y_flux_q(uU, W[RX]), uD,
+                             uc, uU, SY[-RX], SY[0], SY[RX]);
+  const float4 az = hll_axis(z_flux_q(um, qm), z_flux_q(uc, qc), z_flux_q(up, qp), um, uc, up,
+                             szm, SZ[0], szp);
+  return make_float4(uc.x - lam * ((ax.x + ay.x) + az.x), uc.y - lam * ((ax.y + ay.y) + az.y),
+                     uc.z - lam * ((ax.z + ay.z) + az.z), uc.w - lam * ((ax.w + ay.w) + az.w));
+}
+
 // Chemistry of the transported cell, its tallies and the store of the new state (physical F:
 // the chemistry scales F / c by its photon ratio times c).
 template <bool STD>

@@ -85,7 +85,7 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-template <int TY>
+template <int TY, bool HLL = false>
 struct Layout {
   static constexpr int PL = kBoxX * (TY + 2);             // floats per field-plane (with halo)
   static constexpr int PLP = (PL + 31) & ~31;             // padded to 128 bytes
@@ -94,7 +94,8 @@ struct Layout {
   static constexpr int PLR = RX * (TY + 2);               // ring slots per plane
   static constexpr unsigned U_BYTES = 4u * PL * 4u;       // bytes landed per plane (u)
   static constexpr size_t STAGE_BYTES = (size_t)kStages * STAGE * 4;
-  static constexpr size_t RING_BYTES = (size_t)3 * PLR * (16 + 8);
+  // per slot: (N, F/c), the closure pair, and with HLL the x, y, z speed bounds
+  static constexpr size_t RING_BYTES = (size_t)3 * PLR * (16 + 8 + (HLL ? 24 : 0));
   static constexpr size_t BYTES = STAGE_BYTES + RING_BYTES + kStages * 8 + 128;
 };
 
@@ -103,11 +104,12 @@ struct Layout {
 // (no minimum-blocks bound: the compiler's own allocation at TY = 4, 72 registers and seven
 // CTAs per SM, is the fastest configuration; a cap at 64 for eight CTAs spilled and ran slower)
 // FULL: every tile lies inside the grid (nx a multiple of 32, ny of TY), so every thread owns a
-// cell and no own slot needs patching; the bounds tests fold away.
-template <int TY, bool PER, bool STD, bool FULL>
+// cell and no own slot needs patching; the bounds tests fold away. HLL: the HLL intercell flux
+// instead of global Lax-Friedrichs (the ring then also holds each cell's speed bounds).
+template <int TY, bool PER, bool STD, bool FULL, bool HLL = false>
 __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
                                                            const __grid_constant__ TmaMaps M) {
-  using L = Layout<TY>;
+  using L = Layout<TY, HLL>;
   constexpr int TX = kTileX, NH = 2 * TX + 2 * TY;
   extern __shared__ __align__(128) float sm_raw[];
   // 128-byte aligned base for the TMA boxes, as an offset from the shared array (so every
@@ -117,7 +119,11 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
   // ring of prepared planes: (N, Fx/c, Fy/c, Fz/c) and the closure pair (iso, w)
   float4* RU = reinterpret_cast<float4*>(sm + kStages * L::STAGE);
   float2* RW = reinterpret_cast<float2*>(RU + 3 * L::PLR);
-  unsigned long long* full = reinterpret_cast<unsigned long long*>(RW + 3 * L::PLR);
+  // speed bounds (lo, hi) along x, y, z (HLL only; empty otherwise)
+  float2* SX = RW + 3 * L::PLR;
+  float2* SY = SX + (HLL ? 3 * L::PLR : 0);
+  float2* SZ = SY + (HLL ? 3 * L::PLR : 0);
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(SZ + (HLL ? 3 * L::PLR : 0));
 
   const StepParams& P = A.P;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
@@ -193,6 +199,7 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
   };
   // the prepared slot into ring plane r; returns the z flux (Fz/c, Dxz, Dyz, Dzz) N
   auto put = [&](int r, int rslot, const float4& u) {
+    if (HLL) ring_put_speeds(SX + r * L::PLR, SY + r * L::PLR, SZ + r * L::PLR, rslot, u);
     return ring_put(RU + r * L::PLR, RW + r * L::PLR, rslot, u);
   };
 
@@ -242,8 +249,15 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
     if (act) {
       const int c0 = rk * L::PLR + orslot, cm = rkm * L::PLR + orslot;
       const float4 uc = RU[c0], um = RU[cm];
-      const float4 pm = z_flux_q(um, RW[cm]);
-      float4 u = lf_update(RU + c0, RW + c0, uc, um, pm, up, pp, cu, hl);
+      float4 u;
+      if (HLL) {
+        const int cp = rkn * L::PLR + orslot;
+        u = hll_update(RU + c0, RW + c0, SX + c0, SY + c0, SZ + c0, uc, um, RW[cm], SZ[cm], up,
+                       RW[cp], SZ[cp], lam);
+      } else {
+        const float4 pm = z_flux_q(um, RW[cm]);
+        u = lf_update(RU + c0, RW + c0, uc, um, pm, up, pp, cu, hl);
+      }
       if (!PER) {
         float e = 0.f;
         if (gx == 0) e -= uc.y;
@@ -288,8 +302,12 @@ cudaError_t set_tma_attr() {
   e = cudaFuncSetAttribute(k_fused_tma<TY, PER, true, false>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Layout<TY>::BYTES);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_fused_tma<TY, PER, true, true>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Layout<TY>::BYTES);
+  e = cudaFuncSetAttribute(k_fused_tma<TY, PER, true, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Layout<TY>::BYTES);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_fused_tma<TY, PER, false, false, true>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)Layout<TY, true>::BYTES);
 }
 
 template <int TY, bool PER>
@@ -297,7 +315,9 @@ cudaError_t launch_tma_t(const FusedArgs& a, const TmaMaps& m, cudaStream_t s) {
   dim3 grid((a.P.nx + kTileX - 1) / kTileX, (a.P.ny + TY - 1) / TY, (a.P.nz + a.tz - 1) / a.tz);
   dim3 block(kTileX, TY);
   const bool full = a.P.nx % kTileX == 0 && a.P.ny % TY == 0;
-  if (!standard_chemistry(a.P))
+  if (a.P.hll)
+    k_fused_tma<TY, PER, false, false, true><<<grid, block, Layout<TY, true>::BYTES, s>>>(a, m);
+  else if (!standard_chemistry(a.P))
     k_fused_tma<TY, PER, false, false><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);
   else if (full)
     k_fused_tma<TY, PER, true, true><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);

@@ -339,13 +339,13 @@ def test_clumping_chemistry_matches_the_oracle(small, small_oracle, mode):
 @pytest.mark.parametrize("mode", [A.MODE_FUSED, A.MODE_UNFUSED])
 def test_hll_flux_matches_the_oracle(small, small_oracle, mode):
     """The HLL intercell flux (section 2.2) with the M1 wave-speed bounds: parity with the
-    oracle's HLL step; it runs through the plain step whatever the mode, and it differs from the
-    Lax-Friedrichs result well beyond the gates."""
+    oracle's HLL step, in the TMA-staged fused kernel (one launch) and in the plain step; it
+    differs from the Lax-Friedrichs result well beyond the gates."""
     st, idx, rate, run = small
     orc, ob, _ = run_oracle(st, idx, rate, run, 100, flux=1)
     a = A.from_workload(st, idx, rate, run, flux=A.FLUX_HLL)
     a.set_exec(mode, 100)
-    assert a.launches_per_step() == 3
+    assert a.launches_per_step() == (1 if mode == A.MODE_FUSED else 3)
     a.step(100)
     assert a.synchronize() == 0
     f = a.get_fields()
@@ -359,6 +359,26 @@ def test_hll_flux_matches_the_oracle(small, small_oracle, mode):
     glf = small_oracle[0]
     m = glf["N"] > 1e-6 * glf["N"].max()
     assert np.max(np.abs(orc["N"][m] / glf["N"][m] - 1)) > 1e-2
+
+
+@pytest.mark.parametrize("shape,tile", [((20, 24, 36), (4, 64)), ((9, 13, 44), (8, 5)),
+                                        ((12, 40, 96), (16, 7))])
+@pytest.mark.parametrize("bc", ["periodic", "transmissive"])
+def test_hll_fused_equals_plain_hll_closely(shape, tile, bc):
+    """The fused HLL kernel (closure pair and speed bounds shared through the ring) and the
+    plain HLL step (every neighbour's closure and speeds recomputed) do the same arithmetic up
+    to rounding: equal to 1e-5 after 20 steps, tallies alike."""
+    st, idx, rate, run = W.workload_small(shape=shape, nsrc=3, seed_field=51, seed_src=52)
+    r = dict(run, bc=bc)
+    f1, b1, d1, rc1 = run_gpu(st, idx, rate, r, 20, mode=A.MODE_FUSED, tile=tile, flux=A.FLUX_HLL)
+    f2, b2, d2, rc2 = run_gpu(st, idx, rate, r, 20, mode=A.MODE_UNFUSED, flux=A.FLUX_HLL)
+    assert rc1 == 0 and rc2 == 0
+    for k in ("N", "Fx", "Fy", "Fz", "y", "T"):
+        scale = np.abs(f2[k]).max()
+        assert np.abs(f1[k] - f2[k]).max() <= 1e-5 * scale, (bc, k)
+    assert b1["absorbed"] == pytest.approx(b2["absorbed"], rel=1e-5)
+    assert b1["escaped"] == pytest.approx(b2["escaped"], rel=1e-5, abs=1e-9 * b2["emitted"])
+    assert abs(budget_closure(b1)) <= 1e-6
 
 
 def test_hll_stromgren_transmissive_escape():
