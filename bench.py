@@ -35,9 +35,9 @@ HBM_FALLBACK_GBS = 6400.0
 # DRAM bytes per cell-update of the fused kernel from an ncu capture, keyed by the hash of the
 # kernel sources it was taken on (the figure is dropped when the kernel changes).
 NCU_TRAFFIC = {
-    # k_fused_tma, tile 32x4x64, lognormal 256^3: dram__bytes_read.sum 487.49 MB +
-    # dram__bytes_write.sum 363.13 MB per launch over 16,777,216 cells
-    "f4cb6172e03b": (487.488256e6 + 363.130880e6) / 16777216,
+    # k_fused_tma, tile 32x4x64, lognormal 256^3: dram__bytes_read.sum 486.51 MB +
+    # dram__bytes_write.sum 362.43 MB per launch over 16,777,216 cells
+    "39f8acbedd89": (486.513920e6 + 362.430208e6) / 16777216,
 }
 
 
