@@ -38,6 +38,26 @@ def test_collisional_ionisation_matches_independent_fit():
         assert O.beta_coll(T) == pytest.approx(ref, rel=tol), T
 
 
+def test_collisional_excitation_cooling_matches_collision_strengths():
+    """Cen (1992) H I collisional-excitation cooling against the energy lost through the
+    1s -> 2s and 1s -> 2p excitations computed from tabulated effective collision strengths,
+    E12 q12 with q12 = 8.629e-6 Upsilon exp(-E12/kT) / (g1 sqrt(T)). The fit also holds the
+    (smaller) excitations to n >= 3, so it lies at or a little above the n = 2 sum: the ratio
+    stays within [0.8, 1.3] from 5000 K to 20000 K. Over that range the Boltzmann factor alone
+    changes by eight decades, so a wrong threshold temperature, prefactor or temperature
+    divisor leaves the window."""
+    kev = 8.617333262e-5
+    e12 = 10.20                      # eV
+    ratios = []
+    for T, u2s, u2p in _table("hi_collision_strengths.txt"):
+        T = float(T)
+        q12 = 8.629e-6 / (2.0 * math.sqrt(T)) * (float(u2s) + float(u2p)) * math.exp(-e12 / (kev * T))
+        ratios.append(O.cool_coll_exc(T) / (e12 * EV * q12))
+    assert all(0.8 <= r <= 1.3 for r in ratios), ratios
+    # the n >= 3 share grows with temperature: the ratio does not fall from 5000 K to 20000 K
+    assert ratios[-1] >= ratios[0]
+
+
 def test_bremsstrahlung_gaunt_factor_in_textbook_range():
     # free-free emissivity 1.42e-27 g sqrt(T) n_e n_p with a Gaunt factor of order 1.1-1.5
     for T in (1e4, 1e5, 1e6, 1e7):
