@@ -178,56 +178,73 @@ def time_oracle(cst, cidx, crate, crun, steps, omp=False):
 
 
 def surrogate_leg(args):
-    """Chemistry surrogate on the 256^3 lognormal workload: trained on pairs of the exact
-    operator from 64^3 boxes with disjoint seeds, then the plain step with and without it from
-    the same state (residual threshold 1e-4, gate 8 sub-steps)."""
+    """Chemistry surrogate inside the fused step at 256^3. The network is trained on pairs of
+    the exact operator from lognormal boxes of the 128^3 recipe (seeds disjoint from the
+    evaluation boxes); then, from the same state, three runs of each evaluation workload: the
+    exact fused step; the fused step with the surrogate (gate 8 sub-steps, residual 1e-4: the
+    kernel lists the selected cells, a second pass runs the network and falls back to the exact
+    operator); and the same with every prediction rejected (the listed cells take the exact
+    operator in the second pass). Exact vs rejected is the cost of listing the cells; rejected
+    vs surrogate is what the network saves on them."""
     import torch
     from paper_1004_2503_b300 import aton as A
     from paper_1004_2503_b300 import surrogate as S
     from paper_1004_2503_b300 import workloads as W
     t0 = time.perf_counter()
-    train_wl = [W.cosmo_box(64, 2.0, 48, s, s + 1000) for s in range(100, 112)]
-    rec = S.collect_pairs(train_wl, steps=120, stride=1, capacity=40_000_000, keep_light=0.01)
+    wl = list(S.training_boxes(range(100, 112), n=64, sigma_ln=1.5, nsrc=8))
+    rec = S.collect_pairs(wl, steps=120, stride=1, capacity=40_000_000, keep_light=0.01)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
     m = A.Mlp(seed=11)
-    S.train(m, rec, train_wl[0][3]["dt"], steps=3000, batch=16384)
-    t_train = time.perf_counter() - t0
-    st, idx, rate, run = W.workload_256()
-    out = {}
-    for name in ("exact", "surrogate"):
-        a = A.from_workload(st, idx, rate, run)
-        s = torch.cuda.Stream()
-        a.set_stream(s)
-        a.set_exec(A.MODE_UNFUSED, args.graph_batch)
-        if name == "surrogate":
-            a.set_surrogate(m, gate_substeps=8.0, residual_max=1e-4)
-        a.step(5)
-        a.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        k = 60
-        e0.record(s)
-        a.step(k)
-        e1.record(s)
-        e1.synchronize()
-        f = a.get_fields()
-        b = a.photon_budget()
-        d = a.diag()
-        a.close()
-        out[name] = dict(ms=e0.elapsed_time(e1) / k, x=f["x"], d=d,
-                         clos=(b["stored0"] + b["emitted"] - b["stored"] - b["absorbed"] -
-                               b["escaped"] - b["clipped"]) / b["emitted"])
-    m.close()
-    ion = lambda f: float(np.sum(st["nH"] * f))   # noqa: E731
-    ex, su = out["exact"], out["surrogate"]
-    return {"workload": "lognormal 256^3 (sigma_ln=2.0, 1024 sources), plain step, 60 steps",
+    S.train(m, rec, wl[0][3]["dt"], steps=3000, batch=16384)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    evals = {"lognormal_256_seed10": (W.workload_256(10, 1010), 5, 100),
+             "stromgren_256": (W.stromgren_256(), 40, 100)}
+    res = {}
+    for wname, ((st, idx, rate, run), warm, k) in evals.items():
+        out = {}
+        for name, resid in (("exact", None), ("surrogate", 1e-4), ("rejected", 0.0)):
+            a = A.from_workload(st, idx, rate, run)
+            s = torch.cuda.Stream()
+            a.set_stream(s)
+            a.set_exec(A.MODE_FUSED, args.graph_batch)
+            a.step(warm)
+            a.synchronize()
+            if resid is not None:
+                a.set_surrogate(m, gate_substeps=8.0, residual_max=resid)
+            d0 = a.diag()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            a.step(k)
+            e1.record(s)
+            e1.synchronize()
+            f = a.get_fields()
+            b = a.photon_budget()
+            d = a.diag()
+            out[name] = dict(ms=e0.elapsed_time(e1) / k, x=f["x"], launches=a.launches_per_step(),
+                             sur=(d["surrogate_cells"] - d0["surrogate_cells"]) / k,
+                             sub=(d["substeps_total"] - d0["substeps_total"]) / (k * st["N"].size),
+                             clos=(b["stored0"] + b["emitted"] - b["stored"] - b["absorbed"] -
+                                   b["escaped"] - b["clipped"]) / b["emitted"])
+            a.close()
+        ion = lambda x: float(np.sum(st["nH"] * x))   # noqa: E731
+        ex, su, rj = out["exact"], out["surrogate"], out["rejected"]
+        res[wname] = {
+            "steps": k, "after_warmup_steps": warm,
             "ms_per_step_exact": ex["ms"], "ms_per_step_surrogate": su["ms"],
-            "speedup": ex["ms"] / su["ms"],
-            "surrogate_cells_per_step": su["d"]["surrogate_cells"] / su["d"]["steps"],
-            "heavy_substeps_per_cell_exact": ex["d"]["substeps_total"] / (ex["d"]["steps"] * st["N"].size),
+            "ms_per_step_listed_exact": rj["ms"], "speedup": ex["ms"] / su["ms"],
+            "launches_per_step": su["launches"],
+            "surrogate_cells_per_step": su["sur"],
+            "substeps_per_cell_update_exact": ex["sub"],
             "ionised_atoms_rel_err": ion(su["x"]) / ion(ex["x"]) - 1,
             "max_abs_dx": float(np.abs(su["x"] - ex["x"]).max()),
-            "budget_closure": su["clos"], "residual_max": 1e-4, "gate_substeps": 8.0,
-            "train_records": int(rec.shape[0]), "train_seconds": t_train}
+            "budget_closure": su["clos"]}
+    m.close()
+    return {"path": "fused step + surrogate pass", "residual_max": 1e-4, "gate_substeps": 8.0,
+            "train_records": int(rec.shape[0]), "pair_collection_seconds": t1 - t0,
+            "train_seconds": t2 - t1, "train_steps": 3000, "batch": 16384, **res}
 
 
 def reference_arm(args, world, rank):

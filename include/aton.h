@@ -97,8 +97,10 @@ typedef struct {
  * C = (1 - mu^2)((3 chi - 1) chi' / f - 2) + 2 chi (1 - 3 mu^2) + 2 chi' f (3 mu^2 - 1)
  * (the roots of the Jacobian's characteristic polynomial besides the transverse speed
  * c (3 chi - 1) mu / (2 f); +-c/sqrt(3) at f = 0, c mu at f = 1). HLL runs in the one-launch
- * fused step in ATON_MODE_FUSED when nx is a multiple of 4, otherwise through the plain
- * (three-kernel) step. */
+ * fused step only in ATON_MODE_FUSED with nx a multiple of 4 (the TMA-staged kernel); with
+ * nx not a multiple of 4, and in ATON_MODE_FUSED_LDG, it falls back to the plain three-kernel
+ * step, with the same results up to rounding. aton_launches_per_step reports which path a
+ * handle takes (1: fused, 3: plain). */
 #define ATON_FLUX_GLF 0
 #define ATON_FLUX_HLL 1
 

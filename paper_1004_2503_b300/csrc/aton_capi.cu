@@ -182,8 +182,9 @@ static StepParams step_params(const aton_ctx* h) {
 }
 
 static int slots_needed(const aton_ctx* h) {
-  // the plain path with the surrogate uses two slot ranges of kPlainBlocks
-  return std::max(fused_tiles(h->nx, h->ny, h->nz, h->ty, h->tz), 2 * kPlainBlocks);
+  // the plain path with the surrogate uses two slot ranges of kPlainBlocks; the fused path one
+  // slot per tile and, with the surrogate, kSurBlocks after them
+  return std::max(fused_tiles(h->nx, h->ny, h->nz, h->ty, h->tz) + kSurBlocks, 2 * kPlainBlocks);
 }
 
 static void free_slots(Slots& s) {
@@ -339,12 +340,15 @@ static int upload_sources(aton_handle h) {
   return ATON_OK;
 }
 
-// Steps that take the plain three-kernel path whatever the execution mode: with the pair sink or
-// the surrogate, and with the HLL flux unless the TMA-staged fused kernel can run it.
+static bool sur_on(const aton_ctx* h) { return h->sur && h->sur_p.enabled; }
+
+// Steps that take the plain three-kernel path whatever the execution mode: with the pair sink,
+// with the HLL flux unless the TMA-staged fused kernel can run it, and with the surrogate unless
+// the TMA-staged fused kernel can list its cells (GLF flux).
 static bool plain_only(const aton_ctx* h) {
-  const bool hll_fused = h->mode == ATON_MODE_FUSED && h->tma_ok[ty_index(h->ty)];
-  return h->sink != nullptr || (h->sur && h->sur_p.enabled) ||
-         (h->prm.flux == ATON_FLUX_HLL && !hll_fused);
+  const bool tma_fused = h->mode == ATON_MODE_FUSED && h->tma_ok[ty_index(h->ty)];
+  return h->sink != nullptr || (h->prm.flux == ATON_FLUX_HLL && !tma_fused) ||
+         (sur_on(h) && (!tma_fused || h->prm.flux == ATON_FLUX_HLL));
 }
 
 static int enqueue_step(aton_handle h, cudaStream_t s) {
@@ -362,8 +366,35 @@ static int enqueue_step(aton_handle h, cudaStream_t s) {
     a.tz = h->tz;
     a.in_buf = h->cur;
     const int ti = ty_index(h->ty);
-    if (h->mode == ATON_MODE_FUSED && h->tma_ok[ti]) e = launch_fused_tma(h->ty, a, h->tma[ti], s);
-    else e = launch_fused(h->ty, a, s);
+    if (sur_on(h)) {
+      // (plain_only routes every other surrogate case to the plain step: here the TMA kernel
+      // with the GLF flux lists the selected cells, and the surrogate pass takes them)
+      a.sur.norm = mlp_norm(h->sur);
+      a.sur.gate = (float)h->sur_p.gate_substeps;
+      a.sur.list = h->sur_list;
+      a.sur.count = h->sur_count;
+      e = cudaMemsetAsync(h->sur_count, 0, sizeof(int), s);
+      if (e == cudaSuccess) e = launch_fused_tma(h->ty, a, h->tma[ti], s);
+      if (e == cudaSuccess) {
+        PlainArgs q{};
+        q.P = a.P;
+        q.in = in; q.out = out;
+        q.y = h->y; q.T = h->T; q.nH = h->nH;
+        q.slots = h->slots;
+        q.sur_img = mlp_image(h->sur);
+        q.sur_norm = a.sur.norm;
+        q.sur_gate = a.sur.gate;
+        q.sur_resid = (float)h->sur_p.residual_max;
+        q.sur_list = h->sur_list;
+        q.sur_count = h->sur_count;
+        q.sur_slot0 = fused_tiles(h->nx, h->ny, h->nz, h->ty, h->tz);
+        e = launch_sur_pass(q, s);
+      }
+    } else if (h->mode == ATON_MODE_FUSED && h->tma_ok[ti]) {
+      e = launch_fused_tma(h->ty, a, h->tma[ti], s);
+    } else {
+      e = launch_fused(h->ty, a, s);
+    }
   } else {
     PlainArgs a{};
     a.P = step_params(h);
@@ -386,6 +417,7 @@ static int enqueue_step(aton_handle h, cudaStream_t s) {
       a.sur_resid = (float)h->sur_p.residual_max;
       a.sur_list = h->sur_list;
       a.sur_count = h->sur_count;
+      a.sur_slot0 = kPlainBlocks;
     }
     e = launch_plain_step(a, s);
     if (h->sink) h->sink_steps += 1;

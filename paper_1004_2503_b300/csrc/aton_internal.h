@@ -52,6 +52,14 @@ struct Fields {
   float* Fz;
 };
 
+// Cells the fused step hands to the surrogate pass (see SurDefer).
+struct SurList {
+  const MlpNorm* norm = nullptr;   // training range of the network
+  float gate = 0.f;                // sub-step estimate at which a cell is offered
+  int* list = nullptr;             // cell indices (capacity ncell)
+  int* count = nullptr;            // number listed (zeroed before the step)
+};
+
 struct FusedArgs {
   StepParams P;
   Fields in, out;
@@ -63,6 +71,7 @@ struct FusedArgs {
   Slots slots;
   int tz;
   int in_buf;   // ping-pong index of `in` (selects the TMA maps)
+  SurList sur;  // (surrogate instance only)
 };
 
 struct PlainArgs {
@@ -85,6 +94,7 @@ struct PlainArgs {
   float sur_gate, sur_resid;
   int* sur_list;        // candidate cells of the step (capacity ncell)
   int* sur_count;       // number of candidates (reset before every chemistry pass)
+  int sur_slot0;        // first tally slot of the surrogate pass
 };
 
 // The standard chemistry configuration (evolving temperature, cooling and collisional
@@ -104,6 +114,8 @@ bool make_tma_maps(int nx, int ny, int nz, int ty, float* const u[2][4], TmaMaps
 cudaError_t launch_fused(int ty, const FusedArgs& a, cudaStream_t s);
 int fused_tiles(int nx, int ny, int nz, int ty, int tz);
 cudaError_t launch_plain_step(const PlainArgs& a, cudaStream_t s);
+// the surrogate pass over the cells a fused step listed (A.out, A.y, A.T hold their state)
+cudaError_t launch_sur_pass(const PlainArgs& a, cudaStream_t s);
 const MlpImage* mlp_image(const struct ::aton_mlp* h);
 const MlpNorm* mlp_norm(const struct ::aton_mlp* h);
 int plain_launches();

@@ -347,19 +347,9 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain_chem_gate(const PlainAr
     float N = A.out.N[id];
     float y = A.y[id], T = A.T[id];
     const float n = __ldg(A.nH + id);
-    const float Gam = P.csig * N;
-    const float ny = Gam * y * P.dt / (P.sub_eps * fmaxf(y, P.y_floor));
-    const float nT = P.fixed_T ? 0.f : Gam * y * P.eheat_K * P.dt / (P.sub_eps * T * 1.5f * (2.f - y));
-    if (fmaxf(ny, nT) >= A.sur_gate) {
-      const MlpNorm& nm = *A.sur_norm;
-      const float f[kMlpIn] = {log10f(n), log10f(fmaxf(y, 1e-10f)), log10f(T), log10f(fmaxf(N, 1e-30f)), l10dt};
-      bool inr = true;
-#pragma unroll
-      for (int i = 0; i < kMlpIn; ++i) inr = inr && f[i] >= nm.in_min[i] && f[i] <= nm.in_max[i];
-      if (inr) {
-        A.sur_list[atomicAdd(A.sur_count, 1)] = (int)id;
-        continue;
-      }
+    if (sur_candidate(P, A.sur_gate, *A.sur_norm, l10dt, n, N, y, T)) {
+      A.sur_list[atomicAdd(A.sur_count, 1)] = (int)id;
+      continue;
     }
     float X = A.out.Fx[id] * P.rc, Y = A.out.Fy[id] * P.rc, Z = A.out.Fz[id] * P.rc;
     const float N0 = N;
@@ -379,7 +369,8 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain_chem_gate(const PlainAr
 // cores; a prediction is accepted only if its photons absorbed per atom, (N - N')/nH, match
 // the atoms ionised, (y - y') plus the recombinations over dt at the mean state, within
 // sur_resid of max(y, 1e-8); rejected cells take the exact operator. Tallies go to the slots
-// after the first pass's.
+// from sur_slot0 on (after the first pass's). The same pass serves the fused step, whose
+// kernel leaves the listed cells transported but without chemistry in A.out.
 __global__ void __launch_bounds__(kPlainThreads) k_plain_chem_sur(const PlainArgs A) {
   __shared__ __align__(16) MlpImage W;
   __shared__ float xs[kPlainThreads / 32][32][8];
@@ -466,10 +457,15 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain_chem_sur(const PlainArg
       __syncwarp();
     }
   }
-  flush_tally<kPlainThreads / 32>(tl, A.slots, kPlainBlocks + blockIdx.x);
+  flush_tally<kPlainThreads / 32>(tl, A.slots, A.sur_slot0 + blockIdx.x);
 }
 
 int plain_launches() { return 3; }
+
+cudaError_t launch_sur_pass(const PlainArgs& a, cudaStream_t s) {
+  k_plain_chem_sur<<<kSurBlocks, kPlainThreads, 0, s>>>(a);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_plain_step(const PlainArgs& a, cudaStream_t s) {
   if (a.P.hll) {

@@ -231,15 +231,59 @@ __device__ __forceinline__ float4 hll_update(const float4* U, const float2* W, c
                      uc.z - lam * ((ax.z + ay.z) + az.z), uc.w - lam * ((ax.w + ay.w) + az.w));
 }
 
+// ---------------------------------------------------------------------------------------
+// Surrogate gate (the learned replacement of the chemistry operator Phi, Appendix Eq. A4): a
+// cell is offered to the network when the exact operator would sub-cycle heavily -- the
+// explicit estimate of its sub-step count from photo-ionisation (Gamma y dt over
+// eps max(y, y_floor)) or from photo-heating (over eps T) is at least `gate` -- and its
+// features (log10 nH, log10 y, log10 T, log10 N, log10 dt) lie inside the training range.
+// The plain step's gate pass and the fused step take the same decision with this function.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ bool sur_candidate(const StepParams& P, float gate, const MlpNorm& nm,
+                                              float l10dt, float n, float N, float y, float T) {
+  const float Gam = P.csig * N;
+  const float ny = Gam * y * P.dt / (P.sub_eps * fmaxf(y, P.y_floor));
+  const float nT = P.fixed_T ? 0.f : Gam * y * P.eheat_K * P.dt / (P.sub_eps * T * 1.5f * (2.f - y));
+  if (!(fmaxf(ny, nT) >= gate)) return false;
+  const float f[kMlpIn] = {log10f(n), log10f(fmaxf(y, 1e-10f)), log10f(T), log10f(fmaxf(N, 1e-30f)), l10dt};
+  bool inr = true;
+#pragma unroll
+  for (int i = 0; i < kMlpIn; ++i) inr = inr && f[i] >= nm.in_min[i] && f[i] <= nm.in_max[i];
+  return inr;
+}
+
+// The fused step's deferral: asked by chem_cell for cells off the one-sub-step shortcut (those
+// take at most one sub-step, below any gate >= 1).
+struct SurDefer {
+  const StepParams& P;
+  const SurList& S;
+  __device__ __forceinline__ bool operator()(float n, float N, float y, float T) const {
+    // (log10 dt on the device, as in the plain gate pass: the same feature bit for bit)
+    return sur_candidate(P, S.gate, *S.norm, log10f(P.dt), n, N, y, T);
+  }
+};
+
 // Chemistry of the transported cell, its tallies and the store of the new state (physical F:
-// the chemistry scales F / c by its photon ratio times c).
-template <bool STD>
+// the chemistry scales F / c by its photon ratio times c). SUR: a cell the surrogate gate
+// selects is stored as transported (N, F; y and T unchanged) and listed for the surrogate pass,
+// which takes its chemistry and tallies.
+template <bool STD, bool SUR = false>
 __device__ __forceinline__ void chem_tally_store(const StepParams& P, Tally& tl, float cn, float4 u,
                                                  float cy, float cT, const Fields& out, float* Yf,
-                                                 float* Tf, long long o) {
+                                                 float* Tf, long long o, const SurList* S = nullptr) {
   float Nn = u.x, Xn = u.y, Yn = u.z, Zn = u.w;
   const float N0 = Nn;
-  const ChemOut co = chem_cell<STD>(P, cn, Nn, Xn, Yn, Zn, cy, cT, P.c);
+  ChemOut co;
+  if (SUR) {
+    co = chem_cell<STD>(P, cn, Nn, Xn, Yn, Zn, cy, cT, P.c, SurDefer{P, *S});
+    if (co.deferred) {
+      out.N[o] = u.x; out.Fx[o] = u.y * P.c; out.Fy[o] = u.z * P.c; out.Fz[o] = u.w * P.c;
+      S->list[atomicAdd(S->count, 1)] = (int)o;
+      return;
+    }
+  } else {
+    co = chem_cell<STD>(P, cn, Nn, Xn, Yn, Zn, cy, cT, P.c);
+  }
   tl.absorbed.add(N0 - Nn);
   tl.sub += co.nsub;
   tl.mx = max(tl.mx, (unsigned)co.nsub);

@@ -105,8 +105,9 @@ struct Layout {
 // CTAs per SM, is the fastest configuration; a cap at 64 for eight CTAs spilled and ran slower)
 // FULL: every tile lies inside the grid (nx a multiple of 32, ny of TY), so every thread owns a
 // cell and no own slot needs patching; the bounds tests fold away. HLL: the HLL intercell flux
-// instead of global Lax-Friedrichs (the ring then also holds each cell's speed bounds).
-template <int TY, bool PER, bool STD, bool FULL, bool HLL = false>
+// instead of global Lax-Friedrichs (the ring then also holds each cell's speed bounds). SUR:
+// cells the surrogate gate selects are stored transported and listed for the surrogate pass.
+template <int TY, bool PER, bool STD, bool FULL, bool HLL = false, bool SUR = false>
 __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
                                                            const __grid_constant__ TmaMaps M) {
   using L = Layout<TY, HLL>;
@@ -274,7 +275,7 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
         src.z = nz;
         if (++sp < se) src = A.tsrc[sp];
       }
-      chem_tally_store<STD>(P, tl, cn, u, cy, cT, A.out, A.y, A.T, o);
+      chem_tally_store<STD, SUR>(P, tl, cn, u, cy, cT, A.out, A.y, A.T, o, &A.sur);
     }
     cy = ny_; cT = nT_; cn = nn_;
     rkm = rk;
@@ -305,6 +306,15 @@ cudaError_t set_tma_attr() {
   e = cudaFuncSetAttribute(k_fused_tma<TY, PER, true, true>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Layout<TY>::BYTES);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_fused_tma<TY, PER, false, false, false, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Layout<TY>::BYTES);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_fused_tma<TY, PER, true, false, false, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Layout<TY>::BYTES);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_fused_tma<TY, PER, true, true, false, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Layout<TY>::BYTES);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_fused_tma<TY, PER, false, false, true>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)Layout<TY, true>::BYTES);
@@ -317,7 +327,14 @@ cudaError_t launch_tma_t(const FusedArgs& a, const TmaMaps& m, cudaStream_t s) {
   const bool full = a.P.nx % kTileX == 0 && a.P.ny % TY == 0;
   if (a.P.hll)
     k_fused_tma<TY, PER, false, false, true><<<grid, block, Layout<TY, true>::BYTES, s>>>(a, m);
-  else if (!standard_chemistry(a.P))
+  else if (a.sur.list) {   // the surrogate instances
+    if (!standard_chemistry(a.P))
+      k_fused_tma<TY, PER, false, false, false, true><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);
+    else if (full)
+      k_fused_tma<TY, PER, true, true, false, true><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);
+    else
+      k_fused_tma<TY, PER, true, false, false, true><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);
+  } else if (!standard_chemistry(a.P))
     k_fused_tma<TY, PER, false, false><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);
   else if (full)
     k_fused_tma<TY, PER, true, true><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);

@@ -80,3 +80,18 @@ def train(mlp, records, dt, steps=2000, batch=8192, lr=1e-3, lr_end=5e-5, heavy_
             hist.append((k, loss))
     mlp.synchronize()
     return hist
+
+
+def train_on_lognormal_boxes(seeds=range(100, 112), n=64, sigma_ln=1.5, nsrc=8, steps=120,
+                             keep_light=0.01, train_steps=3000, batch=16384, capacity=40_000_000,
+                             net_seed=11):
+    """The surrogate of the 256^3 evaluation: pairs of the exact operator from lognormal boxes
+    of the 128^3 recipe (sigma_ln = 1.5, one source per 32^3 cells) at n^3, seeds disjoint from
+    every evaluation box, every heavily sub-cycled record and a `keep_light` share of the
+    others, then `train_steps` Adam steps. Returns (network, number of records, dt)."""
+    wl = list(training_boxes(seeds, n=n, sigma_ln=sigma_ln, nsrc=nsrc))
+    rec = collect_pairs(wl, steps=steps, stride=1, capacity=capacity, keep_light=keep_light)
+    m = A.Mlp(seed=net_seed)
+    dt = wl[0][3]["dt"]
+    train(m, rec, dt, steps=train_steps, batch=batch)
+    return m, int(rec.shape[0]), dt

@@ -169,6 +169,14 @@ def workload_256(seed_field=10, seed_src=11):
     return cosmo_box(256, 2.0, 1024, seed_field, seed_src)
 
 
+def stromgren_256(nH=1e-5, rate=1e52, T0=100.0, x0=1e-4):
+    """The uniform single-source 256^3 box of the surrogate evaluation: cold, nearly neutral
+    gas (the lognormal recipe's T0 and x0) at 4 kpc cells around one bright source (the top of
+    the recipe's luminosity range), transmissive; the front heats gas from 100 K to ~6e4 K,
+    which the exact operator sub-cycles heavily."""
+    return stromgren_box(n=256, L_kpc=4.0 * 256, nH=nH, T0=T0, x0=x0, rate=rate)
+
+
 def workload_small(shape=(20, 24, 36), nsrc=6, sigma_ln=1.5, seed_field=7, seed_src=8,
                    dx_kpc=4.0):
     """Small ragged-shape lognormal box for parity tests (spans several tiles plus a tail)."""

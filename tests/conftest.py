@@ -25,3 +25,14 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def trained_surrogate():
+    """The chemistry surrogate trained on lognormal boxes of the 128^3 recipe (seeds 100-107,
+    disjoint from every evaluation box) by the library's own kernels; shared by the GPU tests
+    of the surrogate in the step."""
+    from paper_1004_2503_b300 import surrogate as S
+    m, nrec, dt = S.train_on_lognormal_boxes(seeds=range(100, 108), steps=80, train_steps=1500)
+    yield m
+    m.close()

@@ -109,28 +109,18 @@ def test_pair_sink_records_match_the_exact_operator():
         assert abs(o["nsub"] - ns) <= max(2, 0.05 * o["nsub"])
 
 
-def _trained_surrogate():
-    # training boxes with seeds disjoint from the evaluation box; all heavily sub-cycled
-    # records kept, 1 % of the single-sub-step ones
-    train_wl = [W.cosmo_box(48, 2.0, 24, s, s + 1000) for s in range(101, 107)]
-    rec = S.collect_pairs(train_wl, steps=80, stride=1, capacity=20_000_000, keep_light=0.01)
-    m = A.Mlp(seed=11)
-    S.train(m, rec, train_wl[0][3]["dt"], steps=1500, batch=16384)
-    return m
-
-
-def test_surrogate_in_the_step_keeps_the_budget_and_tracks_the_exact_path():
-    """At the residual threshold 1e-4 the accepted predictions keep the global ionised atoms
-    within 1e-3 of the exact path and the photon budget closed."""
-    m = _trained_surrogate()
+def test_surrogate_in_the_plain_step_keeps_the_budget_and_tracks_the_oracle(trained_surrogate):
+    """The plain step's gate and surrogate passes (the fused step's are checked in
+    test_gpu_surrogate_step.py): at the residual threshold 1e-4 the accepted predictions keep the
+    absorbed photons and the ionised atoms within 1e-3 of the oracle, the ionised-volume radius
+    within one cell, and the photon budget closed."""
+    from parity_helpers import run_oracle
     st, idx, rate, run = W.cosmo_box(64, 2.0, 64, 201, 202)
-    ref = A.from_workload(st, idx, rate, run)
-    ref.set_exec(A.MODE_UNFUSED, 0)
-    ref.step(40)
-    fr = ref.get_fields()
-    ref.close()
+    orc, ob, _ = run_oracle(st, idx, rate, run, 40)
     a = A.from_workload(st, idx, rate, run)
-    a.set_surrogate(m, gate_substeps=4.0, residual_max=1e-4)
+    a.set_exec(A.MODE_UNFUSED, 0)
+    a.set_surrogate(trained_surrogate, gate_substeps=4.0, residual_max=1e-4)
+    assert a.launches_per_step() == 4
     a.step(40)
     assert a.synchronize() == 0
     f = a.get_fields()
@@ -141,9 +131,10 @@ def test_surrogate_in_the_step_keeps_the_budget_and_tracks_the_exact_path():
             b["clipped"]) / b["emitted"]
     assert abs(clos) <= 1e-6                   # the tally follows whichever path ran
     assert d["surrogate_cells"] > 0
-    ion_ref = float(np.sum(st["nH"] * fr["x"]))
+    assert b["absorbed"] == pytest.approx(ob["absorbed"], rel=1e-3)
+    ion_ref = float(np.sum(st["nH"] * orc["x"]))
     ion = float(np.sum(st["nH"] * f["x"]))
-    vol_ref = float(np.sum(fr["x"]))
+    vol_ref = float(np.sum(orc["x"]))
     vol = float(np.sum(f["x"]))
     # ionised-volume radius in cells
     r_ref, r = ((3 * vol_ref / (4 * np.pi)) ** (1 / 3), (3 * vol / (4 * np.pi)) ** (1 / 3))
@@ -151,7 +142,6 @@ def test_surrogate_in_the_step_keeps_the_budget_and_tracks_the_exact_path():
           "radius cells", r - r_ref)
     assert abs(ion / ion_ref - 1) <= 1e-3
     assert abs(r - r_ref) < 1.0
-    m.close()
 
 
 def test_surrogate_off_or_rejecting_everything_matches_the_exact_path():

@@ -361,15 +361,25 @@ def test_hll_flux_matches_the_oracle(small, small_oracle, mode):
     assert np.max(np.abs(orc["N"][m] / glf["N"][m] - 1)) > 1e-2
 
 
-@pytest.mark.parametrize("shape,tile", [((20, 24, 36), (4, 64)), ((9, 13, 44), (8, 5)),
-                                        ((12, 40, 96), (16, 7))])
+# shapes are (nz, ny, nx): x-ragged tiles (nx a multiple of 4, not of 32) with ny not a
+# multiple of the tile height, a full-width grid with ragged y, and nx = 30 (not a multiple of
+# 4), where fused HLL falls back to the plain three-kernel step
+@pytest.mark.parametrize("shape,tile,launches", [((20, 22, 36), (4, 64), 1),
+                                                 ((9, 13, 44), (8, 5), 1),
+                                                 ((12, 40, 96), (16, 7), 1),
+                                                 ((8, 10, 30), (4, 3), 3)])
 @pytest.mark.parametrize("bc", ["periodic", "transmissive"])
-def test_hll_fused_equals_plain_hll_closely(shape, tile, bc):
+def test_hll_fused_equals_plain_hll_closely(shape, tile, launches, bc):
     """The fused HLL kernel (closure pair and speed bounds shared through the ring) and the
     plain HLL step (every neighbour's closure and speeds recomputed) do the same arithmetic up
-    to rounding: equal to 1e-5 after 20 steps, tallies alike."""
+    to rounding: equal to 1e-5 after 20 steps, tallies alike. Each case checks which path ran."""
     st, idx, rate, run = W.workload_small(shape=shape, nsrc=3, seed_field=51, seed_src=52)
     r = dict(run, bc=bc)
+    a = A.from_workload(st, idx, rate, r, flux=A.FLUX_HLL)
+    a.set_exec(A.MODE_FUSED, 100)
+    a.set_tile(*tile)
+    assert a.launches_per_step() == launches
+    a.close()
     f1, b1, d1, rc1 = run_gpu(st, idx, rate, r, 20, mode=A.MODE_FUSED, tile=tile, flux=A.FLUX_HLL)
     f2, b2, d2, rc2 = run_gpu(st, idx, rate, r, 20, mode=A.MODE_UNFUSED, flux=A.FLUX_HLL)
     assert rc1 == 0 and rc2 == 0
@@ -381,11 +391,21 @@ def test_hll_fused_equals_plain_hll_closely(shape, tile, bc):
     assert abs(budget_closure(b1)) <= 1e-6
 
 
-def test_hll_stromgren_transmissive_escape():
-    st, idx, rate, run = W.workload_32()
+@pytest.mark.parametrize("n,tile", [(32, None), (20, (8, 7))])
+def test_hll_stromgren_transmissive_escape(n, tile):
+    """HLL in the one-launch fused kernel against the oracle's HLL step on the transmissive
+    Stromgren box: the 32^3 box (full tiles) and a 20^3 box with tile height 8 (20 = 2 x 8 + 4:
+    ragged x and y tiles, whose outside slots are patched from the boundary map)."""
+    st, idx, rate, run = W.stromgren_box(n=n, L_kpc=6.6 * n / 32)
     kw = dict(fixed_T=1, coll_ion=0)
     orc, ob, _ = run_oracle(st, idx, rate, run, 100, flux=1, **kw)
-    f, b, d, rc = run_gpu(st, idx, rate, run, 100, flux=A.FLUX_HLL, **kw)
+    a = A.from_workload(st, idx, rate, run, flux=A.FLUX_HLL, **kw)
+    a.set_exec(A.MODE_FUSED, 100)
+    if tile is not None:
+        a.set_tile(*tile)
+    assert a.launches_per_step() == 1
+    a.close()
+    f, b, d, rc = run_gpu(st, idx, rate, run, 100, flux=A.FLUX_HLL, tile=tile, **kw)
     assert rc == 0
     assert_gates(errors(f, orc))
     assert abs(budget_closure(b)) <= 1e-6

@@ -1,0 +1,149 @@
+"""The learned chemistry surrogate inside the fused step (a replacement of the operator Phi,
+Appendix Eq. A4, for cells the exact operator sub-cycles heavily), checked against the FP64
+oracle.
+
+The fused kernel lists the cells the gate selects, stored transported but without chemistry;
+a second pass runs the network for them and accepts a prediction only where its photon
+residual is within the threshold, the exact operator otherwise. Targets of the surrogate: the
+ionisation front within one cell of the oracle's and the global photon budget within 1e-3.
+
+The 256^3 evaluation: lognormal boxes of the 512^3 recipe at 256^3 (sigma_ln = 2.0, 1024
+sources) with field seeds 10, 11, 12, and the uniform single-source 256^3 Stromgren box, the
+network trained on lognormal boxes of the 128^3 recipe with seeds 100-107.
+"""
+import numpy as np
+import pytest
+
+from paper_1004_2503_b300 import aton as A
+from paper_1004_2503_b300 import workloads as W
+
+from parity_helpers import budget_closure, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _dilate(mask, periodic):
+    """Cells within one cell (Chebyshev distance) of a cell of `mask`."""
+    p = np.pad(mask, 1, mode="wrap" if periodic else "edge")
+    out = np.zeros_like(mask)
+    nz, ny, nx = mask.shape
+    for dz in range(3):
+        for dy in range(3):
+            for dx in range(3):
+                out |= p[dz:dz + nz, dy:dy + ny, dx:dx + nx]
+    return out
+
+
+def front_mismatch(x_gpu, x_orc, periodic):
+    """Cells ionised (x > 0.5) on one side only that are more than one cell from the oracle's
+    front: the GPU's ionised region must contain the oracle's eroded by one cell and lie inside
+    it dilated by one cell."""
+    ig, io = x_gpu > 0.5, x_orc > 0.5
+    outside = ig & ~_dilate(io, periodic)
+    inside = ~ig & ~_dilate(~io, periodic)
+    return int(outside.sum() + inside.sum()), int((ig != io).sum())
+
+
+def _run(st, idx, rate, run, steps, mlp=None, residual=1e-4, gate=8.0, mode=A.MODE_FUSED):
+    a = A.from_workload(st, idx, rate, run)
+    try:
+        a.set_exec(mode, 100)
+        if mlp is not None:
+            a.set_surrogate(mlp, gate_substeps=gate, residual_max=residual)
+        launches = a.launches_per_step()
+        a.step(steps)
+        assert a.synchronize() == 0
+        return a.get_fields(), a.photon_budget(), a.diag(), launches
+    finally:
+        a.close()
+
+
+def test_fused_surrogate_lists_cells_and_tracks_the_oracle(trained_surrogate):
+    st, idx, rate, run = W.cosmo_box(64, 2.0, 64, 201, 202)
+    orc, ob, _ = run_oracle(st, idx, rate, run, 40)
+    f, b, d, launches = _run(st, idx, rate, run, 40, trained_surrogate, gate=4.0)
+    assert launches == 2                           # the fused kernel and the surrogate pass
+    assert d["surrogate_cells"] > 0
+    assert abs(budget_closure(b)) <= 1e-6          # the tally follows whichever path ran
+    assert b["absorbed"] == pytest.approx(ob["absorbed"], rel=1e-3)
+    ion, ion_o = float(np.sum(st["nH"] * f["x"])), float(np.sum(st["nH"] * orc["x"]))
+    assert ion == pytest.approx(ion_o, rel=1e-3)
+    bad, diff = front_mismatch(f["x"], orc["x"], periodic=True)
+    print("surrogate cells", d["surrogate_cells"], "ionised atoms rel", ion / ion_o - 1,
+          "front cells off by > 1 cell", bad, "differing", diff)
+    assert bad == 0
+
+
+def test_fused_surrogate_rejecting_everything_is_the_exact_fused_step(trained_surrogate):
+    """With the residual threshold at 0 every listed cell takes the exact operator in the
+    surrogate pass: the fields equal those of the exact fused step up to rounding (the listed
+    cells' flux goes through one more F/c round trip and the generic chemistry instance)."""
+    st, idx, rate, run = W.cosmo_box(64, 2.0, 64, 201, 202)
+    fr, br, dr, _ = _run(st, idx, rate, run, 30)
+    f, b, d, launches = _run(st, idx, rate, run, 30, trained_surrogate, residual=0.0, gate=1.0)
+    assert launches == 2 and d["surrogate_cells"] == 0
+    for k in ("N", "y", "T"):
+        assert np.allclose(f[k], fr[k], rtol=1e-5, atol=0), k
+    assert b["absorbed"] == pytest.approx(br["absorbed"], rel=1e-6)
+    assert d["substeps_total"] == pytest.approx(dr["substeps_total"], rel=1e-6)
+
+
+@pytest.mark.parametrize("seed", [10, 11, 12])
+def test_lognormal_256_against_the_oracle(trained_surrogate, seed):
+    """256^3 lognormal (sigma_ln = 2.0, 1024 sources), 16 steps, fused step with the surrogate,
+    against the oracle's whole-grid run: front within one cell, absorbed photons and ionised
+    atoms within 1e-3, budget closed."""
+    st, idx, rate, run = W.workload_256(seed_field=seed, seed_src=seed + 1000)
+    K = 16
+    orc, ob, _ = run_oracle(st, idx, rate, run, K)
+    f, b, d, launches = _run(st, idx, rate, run, K, trained_surrogate)
+    assert launches == 2
+    assert abs(budget_closure(b)) <= 1e-3
+    assert b["absorbed"] == pytest.approx(ob["absorbed"], rel=1e-3)
+    ion, ion_o = float(np.sum(st["nH"] * f["x"])), float(np.sum(st["nH"] * orc["x"]))
+    assert ion == pytest.approx(ion_o, rel=1e-3)
+    bad, diff = front_mismatch(f["x"], orc["x"], periodic=True)
+    print("seed", seed, "surrogate cells", d["surrogate_cells"], "ionised atoms rel",
+          ion / ion_o - 1, "front cells off by > 1 cell", bad, "differing", diff)
+    assert d["surrogate_cells"] > 0
+    assert bad == 0
+
+
+def test_stromgren_256_front_within_one_cell_of_the_oracle(trained_surrogate):
+    """The uniform single-source 256^3 box, 60 steps. The explicit 7-point update moves
+    information one cell per step, so after K steps every cell farther than K - 1 cells (along
+    any axis) from the source still holds N = 0 and evolves like the untouched gas. The oracle
+    therefore runs on the (2K+3)^3 box around the source, whose transmissive ghost copies equal
+    those untouched neighbours: inside it the oracle's run is that of the whole box. Outside it
+    the GPU's cells must hold N = 0 and the untouched gas's x and T."""
+    st, idx, rate, run = W.stromgren_256()
+    K = 60
+    n = st["N"].shape[0]
+    c = int(idx[0]) % n
+    lo, hi = c - (K + 1), c + K + 2
+    crop = {k: np.ascontiguousarray(v[lo:hi, lo:hi, lo:hi]) for k, v in st.items()}
+    m = hi - lo
+    cidx = np.array([(K + 1) * (1 + m + m * m)], np.int64)
+    crun = dict(run, nx=m, ny=m, nz=m)
+    orc, ob, _ = run_oracle(crop, cidx, rate, crun, K)
+    f, b, d, launches = _run(st, idx, rate, run, K, trained_surrogate)
+    assert launches == 2
+    inner = (slice(lo, hi),) * 3
+    out_mask = np.ones(st["N"].shape, bool)
+    out_mask[inner] = False
+    assert np.all(f["N"][out_mask] == 0)
+    x_far, T_far = orc["x"][0, 0, 0], orc["T"][0, 0, 0]
+    assert np.abs(f["x"][out_mask] - x_far).max() <= 1e-3 * max(x_far, 1e-3)
+    assert np.abs(f["T"][out_mask] / T_far - 1).max() <= 1e-3
+    assert abs(budget_closure(b)) <= 1e-3
+    assert b["absorbed"] == pytest.approx(ob["absorbed"], rel=1e-3)
+    xg = f["x"][inner]
+    bad, diff = front_mismatch(xg, orc["x"], periodic=False)
+    r_g = (3 * np.count_nonzero(xg > 0.5) / (4 * np.pi)) ** (1 / 3)
+    r_o = (3 * np.count_nonzero(orc["x"] > 0.5) / (4 * np.pi)) ** (1 / 3)
+    print("stromgren surrogate cells", d["surrogate_cells"], "front radius", r_g, "oracle", r_o,
+          "front cells off by > 1 cell", bad, "differing", diff)
+    assert r_o > 4.0                      # the front has moved several cells
+    assert abs(r_g - r_o) < 1.0
+    assert bad == 0
+    assert d["surrogate_cells"] > 0
