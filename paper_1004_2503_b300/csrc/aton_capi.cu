@@ -182,9 +182,8 @@ static StepParams step_params(const aton_ctx* h) {
 }
 
 static int slots_needed(const aton_ctx* h) {
-  // the plain path with the surrogate uses two slot ranges of kPlainBlocks; the fused path one
-  // slot per tile and, with the surrogate, kSurBlocks after them
-  return std::max(fused_tiles(h->nx, h->ny, h->nz, h->ty, h->tz) + kSurBlocks, 2 * kPlainBlocks);
+  // the plain path with the surrogate uses two slot ranges of kPlainBlocks
+  return std::max(fused_tiles(h->nx, h->ny, h->nz, h->ty, h->tz), 2 * kPlainBlocks);
 }
 
 static void free_slots(Slots& s) {
@@ -344,7 +343,7 @@ static bool sur_on(const aton_ctx* h) { return h->sur && h->sur_p.enabled; }
 
 // Steps that take the plain three-kernel path whatever the execution mode: with the pair sink,
 // with the HLL flux unless the TMA-staged fused kernel can run it, and with the surrogate unless
-// the TMA-staged fused kernel can list its cells (GLF flux).
+// the TMA-staged fused kernel can run the network (GLF flux).
 static bool plain_only(const aton_ctx* h) {
   const bool tma_fused = h->mode == ATON_MODE_FUSED && h->tma_ok[ty_index(h->ty)];
   return h->sink != nullptr || (h->prm.flux == ATON_FLUX_HLL && !tma_fused) ||
@@ -368,28 +367,12 @@ static int enqueue_step(aton_handle h, cudaStream_t s) {
     const int ti = ty_index(h->ty);
     if (sur_on(h)) {
       // (plain_only routes every other surrogate case to the plain step: here the TMA kernel
-      // with the GLF flux lists the selected cells, and the surrogate pass takes them)
+      // with the GLF flux runs the network for the cells its gate selects)
+      a.sur.img = mlp_image(h->sur);
       a.sur.norm = mlp_norm(h->sur);
       a.sur.gate = (float)h->sur_p.gate_substeps;
-      a.sur.list = h->sur_list;
-      a.sur.count = h->sur_count;
-      e = cudaMemsetAsync(h->sur_count, 0, sizeof(int), s);
-      if (e == cudaSuccess) e = launch_fused_tma(h->ty, a, h->tma[ti], s);
-      if (e == cudaSuccess) {
-        PlainArgs q{};
-        q.P = a.P;
-        q.in = in; q.out = out;
-        q.y = h->y; q.T = h->T; q.nH = h->nH;
-        q.slots = h->slots;
-        q.sur_img = mlp_image(h->sur);
-        q.sur_norm = a.sur.norm;
-        q.sur_gate = a.sur.gate;
-        q.sur_resid = (float)h->sur_p.residual_max;
-        q.sur_list = h->sur_list;
-        q.sur_count = h->sur_count;
-        q.sur_slot0 = fused_tiles(h->nx, h->ny, h->nz, h->ty, h->tz);
-        e = launch_sur_pass(q, s);
-      }
+      a.sur.resid = (float)h->sur_p.residual_max;
+      e = launch_fused_tma(h->ty, a, h->tma[ti], s);
     } else if (h->mode == ATON_MODE_FUSED && h->tma_ok[ti]) {
       e = launch_fused_tma(h->ty, a, h->tma[ti], s);
     } else {
@@ -417,7 +400,6 @@ static int enqueue_step(aton_handle h, cudaStream_t s) {
       a.sur_resid = (float)h->sur_p.residual_max;
       a.sur_list = h->sur_list;
       a.sur_count = h->sur_count;
-      a.sur_slot0 = kPlainBlocks;
     }
     e = launch_plain_step(a, s);
     if (h->sink) h->sink_steps += 1;
@@ -1075,11 +1057,13 @@ int aton_last_error_cells(aton_handle h, int64_t* count) {
 int aton_launches_per_step(aton_handle h, int* launches) {
   if (int rc = check_h(h)) return rc;
   if (!launches) return fail(ATON_ERR_BADARG, "launches is NULL");
-  if (h->mode == ATON_MODE_FUSED || h->mode == ATON_MODE_FUSED_LDG) *launches = 1;
-  else *launches = h->src_n > 0 ? plain_launches() : plain_launches() - 1;
-  if (plain_only(h) && *launches == 1)
+  const bool fused = (h->mode == ATON_MODE_FUSED || h->mode == ATON_MODE_FUSED_LDG) && !plain_only(h);
+  if (fused) {
+    *launches = 1;   // (with the surrogate the fused kernel runs the network itself)
+  } else {
     *launches = h->src_n > 0 ? plain_launches() : plain_launches() - 1;
-  if (h->sur && h->sur_p.enabled) *launches += 1;   // the candidate pass (plus a counter reset)
+    if (sur_on(h)) *launches += 1;   // the candidate pass (plus a counter reset)
+  }
   return ATON_OK;
 }
 

@@ -227,14 +227,17 @@ __device__ __forceinline__ float cooling_K(float T, float l, float l2T, float rT
 struct ChemOut {
   int nsub;
   int err;
-  int deferred = 0;   // the cell was handed to a later pass (state untouched)
+  int deferred = 0;   // the cell was handed to a later pass (its state untouched)
 };
 
-// Hook of chem_cell for cells that leave the closed-form one-sub-step path: returning true
-// hands the cell to a later pass (the surrogate pass of the fused step) with its state
-// untouched. The default hands nothing on.
+// Hook of chem_cell for a cell that does not take the one-sub-step shortcut: returning true
+// hands the cell, with its state untouched, to a later pass (the surrogate's, in the fused
+// kernel). The default hands nothing on.
 struct NoDefer {
-  __device__ __forceinline__ bool operator()(float, float, float, float) const { return false; }
+  __device__ __forceinline__ bool operator()(float, float, float, float, float, float,
+                                             float) const {
+    return false;
+  }
 };
 
 // STD selects the standard configuration at compile time (evolving temperature with cooling
@@ -242,7 +245,7 @@ struct NoDefer {
 // the kernels take it when the step's parameters are that configuration.
 // F (any units) decays with N; fs is an extra factor applied with that ratio (a unit change the
 // caller wants on the way out, e.g. c to turn F / c back into F).
-// `defer(n, N, y, T)` is asked once for a cell that does not take the one-sub-step shortcut.
+// `defer(n, N, fx, fy, fz, y, T)` is asked once for a cell off the one-sub-step shortcut.
 template <bool STD = false, class Defer = NoDefer>
 __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float& N, float& fx,
                                              float& fy, float& fz, float& y, float& T,
@@ -314,7 +317,7 @@ __device__ __forceinline__ ChemOut chem_cell(const StepParams& P, float n, float
       return ChemOut{1, 0};
     }
   }
-  if (defer(n, Nc, yc, Tc)) return ChemOut{0, 0, 1};
+  if (defer(n, Nc, fx, fy, fz, yc, Tc)) return ChemOut{0, 0, 1};
   while (rh > 0.f) {
     if (o.nsub >= P.max_sub) {
       o.err = 1;

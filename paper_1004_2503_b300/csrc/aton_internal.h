@@ -52,12 +52,12 @@ struct Fields {
   float* Fz;
 };
 
-// Cells the fused step hands to the surrogate pass (see SurDefer).
+// The chemistry surrogate in the fused kernel (surrogate instance only).
 struct SurList {
-  const MlpNorm* norm = nullptr;   // training range of the network
+  const MlpImage* img = nullptr;   // BF16 weight image of the network (device)
+  const MlpNorm* norm = nullptr;   // normalisation and training range (device)
   float gate = 0.f;                // sub-step estimate at which a cell is offered
-  int* list = nullptr;             // cell indices (capacity ncell)
-  int* count = nullptr;            // number listed (zeroed before the step)
+  float resid = 0.f;               // photon residual up to which a prediction is accepted
 };
 
 struct FusedArgs {
@@ -71,7 +71,7 @@ struct FusedArgs {
   Slots slots;
   int tz;
   int in_buf;   // ping-pong index of `in` (selects the TMA maps)
-  SurList sur;  // (surrogate instance only)
+  SurList sur;  // (surrogate instance only: img != nullptr)
 };
 
 struct PlainArgs {
@@ -94,7 +94,6 @@ struct PlainArgs {
   float sur_gate, sur_resid;
   int* sur_list;        // candidate cells of the step (capacity ncell)
   int* sur_count;       // number of candidates (reset before every chemistry pass)
-  int sur_slot0;        // first tally slot of the surrogate pass
 };
 
 // The standard chemistry configuration (evolving temperature, cooling and collisional
@@ -114,8 +113,6 @@ bool make_tma_maps(int nx, int ny, int nz, int ty, float* const u[2][4], TmaMaps
 cudaError_t launch_fused(int ty, const FusedArgs& a, cudaStream_t s);
 int fused_tiles(int nx, int ny, int nz, int ty, int tz);
 cudaError_t launch_plain_step(const PlainArgs& a, cudaStream_t s);
-// the surrogate pass over the cells a fused step listed (A.out, A.y, A.T hold their state)
-cudaError_t launch_sur_pass(const PlainArgs& a, cudaStream_t s);
 const MlpImage* mlp_image(const struct ::aton_mlp* h);
 const MlpNorm* mlp_norm(const struct ::aton_mlp* h);
 int plain_launches();

@@ -340,14 +340,13 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain_chem(const PlainArgs A)
 __global__ void __launch_bounds__(kPlainThreads) k_plain_chem_gate(const PlainArgs A) {
   const StepParams& P = A.P;
   const long long ncell = (long long)P.nx * P.ny * P.nz;
-  const float l10dt = log10f(P.dt);
   Tally tl;
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < ncell;
        id += (long long)gridDim.x * blockDim.x) {
     float N = A.out.N[id];
     float y = A.y[id], T = A.T[id];
     const float n = __ldg(A.nH + id);
-    if (sur_candidate(P, A.sur_gate, *A.sur_norm, l10dt, n, N, y, T)) {
+    if (sur_candidate(P, A.sur_gate, *A.sur_norm, n, N, y, T)) {
       A.sur_list[atomicAdd(A.sur_count, 1)] = (int)id;
       continue;
     }
@@ -368,9 +367,8 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain_chem_gate(const PlainAr
 // Pass 2: the listed candidates, 32 per warp. The warp runs the MLP for its 32 cells on tensor
 // cores; a prediction is accepted only if its photons absorbed per atom, (N - N')/nH, match
 // the atoms ionised, (y - y') plus the recombinations over dt at the mean state, within
-// sur_resid of max(y, 1e-8); rejected cells take the exact operator. Tallies go to the slots
-// from sur_slot0 on (after the first pass's). The same pass serves the fused step, whose
-// kernel leaves the listed cells transported but without chemistry in A.out.
+// sur_resid of max(y, 1e-8) (sur_accept); rejected cells take the exact operator. Tallies go to
+// the slots after the first pass's.
 __global__ void __launch_bounds__(kPlainThreads) k_plain_chem_sur(const PlainArgs A) {
   __shared__ __align__(16) MlpImage W;
   __shared__ float xs[kPlainThreads / 32][32][8];
@@ -424,18 +422,9 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain_chem_sur(const PlainArg
       __syncwarp();
       bool done = false;
       if (valid) {
-        const float dly = fminf(fmaxf(nm.out_mean[0] + ys[w][lane][0] / nm.out_scale[0], -kDlyMax), kDlyMax);
-        const float dlT = fminf(fmaxf(nm.out_mean[1] + ys[w][lane][1] / nm.out_scale[1], -kDlTMax), kDlTMax);
-        const float dlN = fminf(fmaxf(nm.out_mean[2] + ys[w][lane][2] / nm.out_scale[2], -kDlNMax), 0.f);
-        const float y1 = fminf(fmaxf(fmaxf(y, 1e-10f) * exp2f(3.321928f * dly), 0.f), 1.f);
-        const float T1 = fmaxf(T * exp2f(3.321928f * dlT), P.T_floor);
-        const float N1 = fminf(fmaxf(N, 1e-30f) * exp2f(3.321928f * dlN), N);
-        // photon-conservation residual
-        const float xm = 1.f - 0.5f * (y + y1);
-        const float am = alpha_B(kLog2TwoTHI - log2f(0.5f * (T + T1)));
-        const float rec = am * n * xm * xm * P.dt;
-        const float r = fabsf((N - N1) / n - ((y - y1) + rec)) / fmaxf(y, 1e-8f);
-        if (r <= A.sur_resid && isfinite(y1) && isfinite(T1) && isfinite(N1)) {
+        const float o3[3] = {ys[w][lane][0], ys[w][lane][1], ys[w][lane][2]};
+        float N1, y1, T1;
+        if (sur_accept(P, nm, A.sur_resid, o3, n, N, y, T, N1, y1, T1)) {
           const float fr = N > 0.f ? N1 / N : 1.f;
           N = N1; X *= fr; Y *= fr; Z *= fr; y = y1; T = T1;
           done = true;
@@ -457,15 +446,10 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain_chem_sur(const PlainArg
       __syncwarp();
     }
   }
-  flush_tally<kPlainThreads / 32>(tl, A.slots, A.sur_slot0 + blockIdx.x);
+  flush_tally<kPlainThreads / 32>(tl, A.slots, kPlainBlocks + blockIdx.x);
 }
 
 int plain_launches() { return 3; }
-
-cudaError_t launch_sur_pass(const PlainArgs& a, cudaStream_t s) {
-  k_plain_chem_sur<<<kSurBlocks, kPlainThreads, 0, s>>>(a);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_plain_step(const PlainArgs& a, cudaStream_t s) {
   if (a.P.hll) {

@@ -143,4 +143,59 @@ __device__ __forceinline__ void mlp_forward16(const MlpImage& W, const unsigned 
   for (int ks = 0; ks < 4; ++ks) mma_bf16(y, ha[ks], ld_pair(w + ks * 16), ld_pair(w + ks * 16 + 8));
 }
 
+// Inference of 16 rows with few registers (bitwise the outputs of mlp_forward16: the same
+// products in the same order): the activations of each layer go to a per-warp shared-memory
+// tile H (16 rows x kP2 BF16, twice: layer 1 and layer 2) instead of registers, and the output
+// tiles are not unrolled, so only one accumulator tile and one operand set are live. For the
+// fused step kernel, whose register count the rarely used network must not raise. W may sit in
+// global memory (read through L1).
+__device__ __forceinline__ void mlp_infer16_sh(const MlpImage& W, const unsigned xa[4],
+                                               __nv_bfloat16* H1, __nv_bfloat16* H2, float y[4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  // C tile (rows g, g+8; columns col, col+1) after SiLU into H as BF16 pairs
+  auto put = [&](__nv_bfloat16* H, int col, const float c[4]) {
+    *reinterpret_cast<unsigned*>(H + g * kP2 + col) = pack_bf16(silu(c[0]), silu(c[1]));
+    *reinterpret_cast<unsigned*>(H + (g + 8) * kP2 + col) = pack_bf16(silu(c[2]), silu(c[3]));
+  };
+  // A fragment of k step ks from H
+  auto frag = [&](const __nv_bfloat16* H, int ks, unsigned a[4]) {
+    const int c = ks * 16 + 2 * t;
+    a[0] = ld_pair(H + g * kP2 + c);
+    a[1] = ld_pair(H + (g + 8) * kP2 + c);
+    a[2] = ld_pair(H + g * kP2 + c + 8);
+    a[3] = ld_pair(H + (g + 8) * kP2 + c + 8);
+  };
+#pragma unroll 1
+  for (int nt = 0; nt < 8; ++nt) {
+    const int col = nt * 8 + 2 * t;
+    float acc[4] = {W.b1[col], W.b1[col + 1], W.b1[col], W.b1[col + 1]};
+    mma_bf16(acc, xa, ld_pair(W.W1 + (nt * 8 + g) * kP1 + 2 * t), 0u);
+    put(H1, col, acc);
+  }
+  __syncwarp();
+#pragma unroll 1
+  for (int nt = 0; nt < 8; ++nt) {
+    const int col = nt * 8 + 2 * t;
+    float acc[4] = {W.b2[col], W.b2[col + 1], W.b2[col], W.b2[col + 1]};
+    const __nv_bfloat16* w = W.W2 + (nt * 8 + g) * kP2 + 2 * t;
+#pragma unroll 1
+    for (int ks = 0; ks < 4; ++ks) {
+      unsigned a[4];
+      frag(H1, ks, a);
+      mma_bf16(acc, a, ld_pair(w + ks * 16), ld_pair(w + ks * 16 + 8));
+    }
+    put(H2, col, acc);
+  }
+  __syncwarp();
+  y[0] = W.b3[2 * t]; y[1] = W.b3[2 * t + 1]; y[2] = y[0]; y[3] = y[1];
+  const __nv_bfloat16* w = W.W3 + g * kP2 + 2 * t;
+#pragma unroll 1
+  for (int ks = 0; ks < 4; ++ks) {
+    unsigned a[4];
+    frag(H2, ks, a);
+    mma_bf16(y, a, ld_pair(w + ks * 16), ld_pair(w + ks * 16 + 8));
+  }
+  __syncwarp();   // (H may be reused by the warp's next call)
+}
+
 }  // namespace aton

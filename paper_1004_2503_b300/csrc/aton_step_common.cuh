@@ -232,57 +232,145 @@ __device__ __forceinline__ float4 hll_update(const float4* U, const float2* W, c
 }
 
 // ---------------------------------------------------------------------------------------
-// Surrogate gate (the learned replacement of the chemistry operator Phi, Appendix Eq. A4): a
-// cell is offered to the network when the exact operator would sub-cycle heavily -- the
-// explicit estimate of its sub-step count from photo-ionisation (Gamma y dt over
-// eps max(y, y_floor)) or from photo-heating (over eps T) is at least `gate` -- and its
-// features (log10 nH, log10 y, log10 T, log10 N, log10 dt) lie inside the training range.
-// The plain step's gate pass and the fused step take the same decision with this function.
+// Learned chemistry surrogate (a replacement of the operator Phi, Appendix Eq. A4, for cells
+// the exact operator sub-cycles heavily).
+//
+// Gate: a cell is offered to the network when the explicit estimate of its sub-step count from
+// photo-ionisation (Gamma y dt over eps max(y, y_floor)) or from photo-heating (over eps T) is
+// at least `gate` -- written without quotients -- and its features (log10 nH, log10 y, log10 T,
+// log10 N, log10 dt) lie inside the training range. The plain step's gate pass and the fused
+// kernel take the same decision with this function.
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ bool sur_candidate(const StepParams& P, float gate, const MlpNorm& nm,
-                                              float l10dt, float n, float N, float y, float T) {
-  const float Gam = P.csig * N;
-  const float ny = Gam * y * P.dt / (P.sub_eps * fmaxf(y, P.y_floor));
-  const float nT = P.fixed_T ? 0.f : Gam * y * P.eheat_K * P.dt / (P.sub_eps * T * 1.5f * (2.f - y));
-  if (!(fmaxf(ny, nT) >= gate)) return false;
-  const float f[kMlpIn] = {log10f(n), log10f(fmaxf(y, 1e-10f)), log10f(T), log10f(fmaxf(N, 1e-30f)), l10dt};
+                                              float n, float N, float y, float T) {
+  const float gy = P.csig * N * y * P.dt;                  // Gamma y dt
+  const float lim = gate * P.sub_eps;
+  const bool heavy = gy >= lim * fmaxf(y, P.y_floor) ||
+                     (!P.fixed_T && gy * P.eheat_K >= lim * T * 1.5f * (2.f - y));
+  if (!heavy) return false;
+  const float f[kMlpIn] = {log10f(n), log10f(fmaxf(y, 1e-10f)), log10f(T), log10f(fmaxf(N, 1e-30f)),
+                           log10f(P.dt)};
   bool inr = true;
 #pragma unroll
   for (int i = 0; i < kMlpIn; ++i) inr = inr && f[i] >= nm.in_min[i] && f[i] <= nm.in_max[i];
   return inr;
 }
 
-// The fused step's deferral: asked by chem_cell for cells off the one-sub-step shortcut (those
-// take at most one sub-step, below any gate >= 1).
+// Decodes the network's normalised outputs o (changes of log10 y, log10 T, log10 N over dt,
+// clipped to their training ranges) into (N', y', T') and accepts them only if the photons
+// absorbed per atom, (N - N')/nH, match the atoms ionised (y - y') plus the recombinations over
+// dt at the mean state within `resid` of max(y, 1e-8).
+__device__ __forceinline__ bool sur_accept(const StepParams& P, const MlpNorm& nm, float resid,
+                                           const float o[3], float n, float N, float y, float T,
+                                           float& N1, float& y1, float& T1) {
+  const float dly = fminf(fmaxf(nm.out_mean[0] + o[0] / nm.out_scale[0], -kDlyMax), kDlyMax);
+  const float dlT = fminf(fmaxf(nm.out_mean[1] + o[1] / nm.out_scale[1], -kDlTMax), kDlTMax);
+  const float dlN = fminf(fmaxf(nm.out_mean[2] + o[2] / nm.out_scale[2], -kDlNMax), 0.f);
+  y1 = fminf(fmaxf(fmaxf(y, 1e-10f) * exp2f(3.321928f * dly), 0.f), 1.f);
+  T1 = fmaxf(T * exp2f(3.321928f * dlT), P.T_floor);
+  N1 = fminf(fmaxf(N, 1e-30f) * exp2f(3.321928f * dlN), N);
+  const float xm = 1.f - 0.5f * (y + y1);
+  const float am = alpha_B(kLog2TwoTHI - log2f(0.5f * (T + T1)));
+  const float rec = am * n * xm * xm * P.dt;
+  const float r = fabsf((N - N1) / n - ((y - y1) + rec)) / fmaxf(y, 1e-8f);
+  return r <= resid && isfinite(y1) && isfinite(T1) && isfinite(N1);
+}
+
+// The network for the cells of one warp (all 32 lanes call this together): the MLP for the
+// warp's 32 cells on tensor cores (two 16-row m16n8k16 passes of mlp_infer16_sh, weights read
+// through L1 from the device image, activations in the warp's shared-memory tiles H1, H2);
+// each lane with `cand` set decodes and checks its own prediction. Returns whether this lane's prediction
+// was accepted (then N1, y1, T1 hold it). Features are exchanged with shuffles: lane (g, t) of a
+// 16-row pass needs features 2t, 2t+1 of rows g and g+8, and a row's three outputs sit in the
+// lanes 4 (row mod 8) and 4 (row mod 8) + 1.
+__device__ __forceinline__ bool sur_warp(const StepParams& P, const SurList& S, bool cand, float n,
+                                         float N, float y, float T, float& N1, float& y1,
+                                         float& T1, __nv_bfloat16* H1, __nv_bfloat16* H2) {
+  const unsigned full = 0xffffffffu;
+  const MlpNorm& nm = *S.norm;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  float f[kMlpIn] = {log10f(n), log10f(fmaxf(y, 1e-10f)), log10f(T), log10f(fmaxf(N, 1e-30f)),
+                     log10f(P.dt)};
+#pragma unroll
+  for (int i = 0; i < kMlpIn; ++i) f[i] = (f[i] - nm.in_mean[i]) * nm.in_scale[i];
+  float o[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    const int ra = half * 16 + g, rb = ra + 8;
+    float fa[kMlpIn], fb[kMlpIn];
+#pragma unroll
+    for (int i = 0; i < kMlpIn; ++i) {
+      fa[i] = __shfl_sync(full, f[i], ra);
+      fb[i] = __shfl_sync(full, f[i], rb);
+    }
+    // columns 2t, 2t+1 of the 16-wide (5 used) input tile
+    const float a0 = t == 0 ? fa[0] : (t == 1 ? fa[2] : (t == 2 ? fa[4] : 0.f));
+    const float a1 = t == 0 ? fa[1] : (t == 1 ? fa[3] : 0.f);
+    const float b0 = t == 0 ? fb[0] : (t == 1 ? fb[2] : (t == 2 ? fb[4] : 0.f));
+    const float b1 = t == 0 ? fb[1] : (t == 1 ? fb[3] : 0.f);
+    const unsigned a[4] = {pack_bf16(a0, a1), pack_bf16(b0, b1), 0u, 0u};
+    float yo[4];
+    mlp_infer16_sh(*S.img, a, H1, H2, yo);
+    const int r = lane - half * 16;
+    const int s0 = 4 * (r & 7);
+    const float c0 = __shfl_sync(full, yo[0], s0), c1 = __shfl_sync(full, yo[1], s0);
+    const float c2 = __shfl_sync(full, yo[2], s0), c3 = __shfl_sync(full, yo[3], s0);
+    const float d0 = __shfl_sync(full, yo[0], s0 + 1), d2 = __shfl_sync(full, yo[2], s0 + 1);
+    if (r >= 0 && r < 16) {
+      const bool hi = r >= 8;
+      o[0] = hi ? c2 : c0;
+      o[1] = hi ? c3 : c1;
+      o[2] = hi ? d2 : d0;
+    }
+  }
+  return cand && sur_accept(P, nm, S.resid, o, n, N, y, T, N1, y1, T1);
+}
+
+// A cell the fused kernel's surrogate gate selected, kept in shared memory until the end of the
+// CTA's z-loop (F as F / c).
+struct SurRec {
+  float N, X, Y, Z, y, T, n;
+  int o;
+};
+constexpr int kSurCap = 64;   // cells per CTA; a cell beyond them takes the exact operator at once
+
+// The fused kernel's deferral (the chem_cell hook): a candidate goes to the CTA's list.
 struct SurDefer {
   const StepParams& P;
   const SurList& S;
-  __device__ __forceinline__ bool operator()(float n, float N, float y, float T) const {
-    // (log10 dt on the device, as in the plain gate pass: the same feature bit for bit)
-    return sur_candidate(P, S.gate, *S.norm, log10f(P.dt), n, N, y, T);
+  SurRec* buf;
+  int* cnt;
+  int o;
+  __device__ __forceinline__ bool operator()(float n, float N, float fx, float fy, float fz,
+                                             float y, float T) const {
+    if (!sur_candidate(P, S.gate, *S.norm, n, N, y, T)) return false;
+    const int k = atomicAdd(cnt, 1);
+    if (k >= kSurCap) return false;
+    buf[k] = SurRec{N, fx, fy, fz, y, T, n, o};
+    return true;
   }
 };
 
 // Chemistry of the transported cell, its tallies and the store of the new state (physical F:
-// the chemistry scales F / c by its photon ratio times c). SUR: a cell the surrogate gate
-// selects is stored as transported (N, F; y and T unchanged) and listed for the surrogate pass,
-// which takes its chemistry and tallies.
-template <bool STD, bool SUR = false>
+// the chemistry scales F / c by its photon ratio times c). With `sur` set the cell takes the
+// network's accepted prediction (N1, y1, T1; F scaled with N) instead of the exact operator.
+// With a deferral `defer` (SurDefer) a selected cell is listed and neither stored nor tallied.
+template <bool STD, class Defer = NoDefer>
 __device__ __forceinline__ void chem_tally_store(const StepParams& P, Tally& tl, float cn, float4 u,
                                                  float cy, float cT, const Fields& out, float* Yf,
-                                                 float* Tf, long long o, const SurList* S = nullptr) {
+                                                 float* Tf, long long o, bool sur = false,
+                                                 float N1 = 0.f, float y1 = 0.f, float T1 = 0.f,
+                                                 const Defer& defer = Defer()) {
   float Nn = u.x, Xn = u.y, Yn = u.z, Zn = u.w;
   const float N0 = Nn;
-  ChemOut co;
-  if (SUR) {
-    co = chem_cell<STD>(P, cn, Nn, Xn, Yn, Zn, cy, cT, P.c, SurDefer{P, *S});
-    if (co.deferred) {
-      out.N[o] = u.x; out.Fx[o] = u.y * P.c; out.Fy[o] = u.z * P.c; out.Fz[o] = u.w * P.c;
-      S->list[atomicAdd(S->count, 1)] = (int)o;
-      return;
-    }
+  ChemOut co{0, 0};
+  if (sur) {
+    const float fr = (N0 > 0.f ? N1 / N0 : 1.f) * P.c;
+    Nn = N1; Xn *= fr; Yn *= fr; Zn *= fr; cy = y1; cT = T1;
+    tl.sur += 1;
   } else {
-    co = chem_cell<STD>(P, cn, Nn, Xn, Yn, Zn, cy, cT, P.c);
+    co = chem_cell<STD>(P, cn, Nn, Xn, Yn, Zn, cy, cT, P.c, defer);
+    if (co.deferred) return;
   }
   tl.absorbed.add(N0 - Nn);
   tl.sub += co.nsub;
@@ -292,6 +380,35 @@ __device__ __forceinline__ void chem_tally_store(const StepParams& P, Tally& tl,
   if (!isfinite(Nn + cT + (Xn + Yn + Zn))) tl.nan += 1;
   out.N[o] = Nn; out.Fx[o] = Xn; out.Fy[o] = Yn; out.Fz[o] = Zn;
   Yf[o] = cy; Tf[o] = cT;
+}
+
+// The end of a fused CTA with the surrogate: its listed cells, 32 per warp (warps 0 and 1),
+// run through the network; accepted predictions are stored, the others take the exact operator
+// (their latency overlaps with the other CTAs on the SM). Called by every thread of the CTA
+// after its z-loop. `scratch`: shared memory free by then (the plane ring), at least
+// 2 x 2 x 16 x kP2 BF16 (9216 bytes).
+constexpr int kSurScratchBytes = 2 * 2 * 16 * kP2 * 2;
+template <bool STD>
+__device__ __forceinline__ void sur_tail(const StepParams& P, const SurList& S, const SurRec* buf,
+                                         const int* cnt, Tally& tl, const Fields& out, float* Yf,
+                                         float* Tf, void* scratch) {
+  static_assert(kSurCap <= 64, "two warps run the list");
+  __syncthreads();
+  const int nc = min(*cnt, kSurCap);
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int w = tid >> 5, lane = tid & 31;
+  if (w < 2 && w * 32 < nc) {   // (uniform within the warp)
+    __nv_bfloat16* H1 = reinterpret_cast<__nv_bfloat16*>(scratch) + w * 2 * 16 * kP2;
+    __nv_bfloat16* H2 = H1 + 16 * kP2;
+    const int k = w * 32 + lane;
+    const bool valid = k < nc;
+    const SurRec r = valid ? buf[k] : SurRec{0.f, 0.f, 0.f, 0.f, 1.f, 1e4f, 1.f, 0};
+    float N1 = 0.f, y1 = 0.f, T1 = 0.f;
+    const bool acc = sur_warp(P, S, valid, r.n, r.N, r.y, r.T, N1, y1, T1, H1, H2);
+    if (valid)
+      chem_tally_store<STD>(P, tl, r.n, make_float4(r.N, r.X, r.Y, r.Z), r.y, r.T, out, Yf, Tf,
+                            r.o, acc, N1, y1, T1);
+  }
 }
 
 }  // namespace aton

@@ -106,7 +106,9 @@ struct Layout {
 // FULL: every tile lies inside the grid (nx a multiple of 32, ny of TY), so every thread owns a
 // cell and no own slot needs patching; the bounds tests fold away. HLL: the HLL intercell flux
 // instead of global Lax-Friedrichs (the ring then also holds each cell's speed bounds). SUR:
-// cells the surrogate gate selects are stored transported and listed for the surrogate pass.
+// the chemistry surrogate; a cell the gate selects (off the one-sub-step shortcut) is listed in
+// shared memory and, after the z-loop, runs through the network (sur_tail), the accepted
+// predictions replacing the exact operator.
 template <int TY, bool PER, bool STD, bool FULL, bool HLL = false, bool SUR = false>
 __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
                                                            const __grid_constant__ TmaMaps M) {
@@ -151,8 +153,11 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
     if (!failed && !mbar_wait(&full[k % kStages], (k / kStages) & 1)) failed = true;
   };
 
+  __shared__ SurRec s_sur[SUR ? kSurCap : 1];   // the CTA's surrogate list
+  __shared__ int s_nsur;
   int issued = 0;   // planes issued so far (thread 0)
   if (tid == 0) {
+    if (SUR) s_nsur = 0;
     for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     for (; issued < kStages && issued < nplanes; ++issued) issue(issued);
@@ -275,7 +280,11 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
         src.z = nz;
         if (++sp < se) src = A.tsrc[sp];
       }
-      chem_tally_store<STD, SUR>(P, tl, cn, u, cy, cT, A.out, A.y, A.T, o, &A.sur);
+      if (SUR)
+        chem_tally_store<STD>(P, tl, cn, u, cy, cT, A.out, A.y, A.T, o, false, 0.f, 0.f, 0.f,
+                              SurDefer{P, A.sur, s_sur, &s_nsur, (int)o});
+      else
+        chem_tally_store<STD>(P, tl, cn, u, cy, cT, A.out, A.y, A.T, o);
     }
     cy = ny_; cT = nT_; cn = nn_;
     rkm = rk;
@@ -289,6 +298,10 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
   if (__syncthreads_or(failed) && tid == 0)
     for (int k = max(0, issued - kStages); k < issued; ++k)
       mbar_wait(&full[k % kStages], (k / kStages) & 1);
+  if (SUR) {
+    static_assert(!SUR || L::RING_BYTES >= kSurScratchBytes, "ring too small for the network");
+    sur_tail<STD>(P, A.sur, s_sur, &s_nsur, tl, A.out, A.y, A.T, RU);
+  }
   flush_tally<TY>(tl, A.slots, tile);
 }
 
@@ -327,7 +340,7 @@ cudaError_t launch_tma_t(const FusedArgs& a, const TmaMaps& m, cudaStream_t s) {
   const bool full = a.P.nx % kTileX == 0 && a.P.ny % TY == 0;
   if (a.P.hll)
     k_fused_tma<TY, PER, false, false, true><<<grid, block, Layout<TY, true>::BYTES, s>>>(a, m);
-  else if (a.sur.list) {   // the surrogate instances
+  else if (a.sur.img) {   // the surrogate instances
     if (!standard_chemistry(a.P))
       k_fused_tma<TY, PER, false, false, false, true><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);
     else if (full)

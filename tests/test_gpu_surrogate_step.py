@@ -2,9 +2,9 @@
 Appendix Eq. A4, for cells the exact operator sub-cycles heavily), checked against the FP64
 oracle.
 
-The fused kernel lists the cells the gate selects, stored transported but without chemistry;
-a second pass runs the network for them and accepts a prediction only where its photon
-residual is within the threshold, the exact operator otherwise. Targets of the surrogate: the
+In the fused kernel a warp holding a cell the gate selects runs the network for its cells on
+tensor cores; a prediction is accepted only where its photon residual is within the threshold,
+and the cell takes the exact operator otherwise (one launch per step). Targets of the surrogate: the
 ionisation front within one cell of the oracle's and the global photon budget within 1e-3.
 
 The 256^3 evaluation: lognormal boxes of the 512^3 recipe at 256^3 (sigma_ln = 2.0, 1024
@@ -58,11 +58,11 @@ def _run(st, idx, rate, run, steps, mlp=None, residual=1e-4, gate=8.0, mode=A.MO
         a.close()
 
 
-def test_fused_surrogate_lists_cells_and_tracks_the_oracle(trained_surrogate):
+def test_fused_surrogate_tracks_the_oracle(trained_surrogate):
     st, idx, rate, run = W.cosmo_box(64, 2.0, 64, 201, 202)
     orc, ob, _ = run_oracle(st, idx, rate, run, 40)
     f, b, d, launches = _run(st, idx, rate, run, 40, trained_surrogate, gate=4.0)
-    assert launches == 2                           # the fused kernel and the surrogate pass
+    assert launches == 1                           # the network runs inside the fused kernel
     assert d["surrogate_cells"] > 0
     assert abs(budget_closure(b)) <= 1e-6          # the tally follows whichever path ran
     assert b["absorbed"] == pytest.approx(ob["absorbed"], rel=1e-3)
@@ -75,17 +75,18 @@ def test_fused_surrogate_lists_cells_and_tracks_the_oracle(trained_surrogate):
 
 
 def test_fused_surrogate_rejecting_everything_is_the_exact_fused_step(trained_surrogate):
-    """With the residual threshold at 0 every listed cell takes the exact operator in the
-    surrogate pass: the fields equal those of the exact fused step up to rounding (the listed
-    cells' flux goes through one more F/c round trip and the generic chemistry instance)."""
+    """With the residual threshold at 0 every prediction is rejected and each offered cell takes
+    the exact operator in place: the fields equal those of the exact fused step (the same
+    arithmetic in the surrogate instance of the kernel; compared to 1e-6 in case the compiler
+    contracts an expression differently there)."""
     st, idx, rate, run = W.cosmo_box(64, 2.0, 64, 201, 202)
     fr, br, dr, _ = _run(st, idx, rate, run, 30)
     f, b, d, launches = _run(st, idx, rate, run, 30, trained_surrogate, residual=0.0, gate=1.0)
-    assert launches == 2 and d["surrogate_cells"] == 0
+    assert launches == 1 and d["surrogate_cells"] == 0
     for k in ("N", "y", "T"):
-        assert np.allclose(f[k], fr[k], rtol=1e-5, atol=0), k
+        assert np.allclose(f[k], fr[k], rtol=1e-6, atol=0), k
     assert b["absorbed"] == pytest.approx(br["absorbed"], rel=1e-6)
-    assert d["substeps_total"] == pytest.approx(dr["substeps_total"], rel=1e-6)
+    assert d["substeps_total"] == dr["substeps_total"]
 
 
 @pytest.mark.parametrize("seed", [10, 11, 12])
@@ -97,7 +98,7 @@ def test_lognormal_256_against_the_oracle(trained_surrogate, seed):
     K = 16
     orc, ob, _ = run_oracle(st, idx, rate, run, K)
     f, b, d, launches = _run(st, idx, rate, run, K, trained_surrogate)
-    assert launches == 2
+    assert launches == 1
     assert abs(budget_closure(b)) <= 1e-3
     assert b["absorbed"] == pytest.approx(ob["absorbed"], rel=1e-3)
     ion, ion_o = float(np.sum(st["nH"] * f["x"])), float(np.sum(st["nH"] * orc["x"]))
@@ -127,7 +128,7 @@ def test_stromgren_256_front_within_one_cell_of_the_oracle(trained_surrogate):
     crun = dict(run, nx=m, ny=m, nz=m)
     orc, ob, _ = run_oracle(crop, cidx, rate, crun, K)
     f, b, d, launches = _run(st, idx, rate, run, K, trained_surrogate)
-    assert launches == 2
+    assert launches == 1
     inner = (slice(lo, hi),) * 3
     out_mask = np.ones(st["N"].shape, bool)
     out_mask[inner] = False
