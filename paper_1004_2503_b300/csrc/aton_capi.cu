@@ -106,6 +106,10 @@ struct aton_ctx {
   aton_surrogate_params sur_p{};
   int* sur_list = nullptr;
   int* sur_count = nullptr;
+  // the fused kernel's per-tile surrogate lists (sized for sur_tiles tiles)
+  SurRec* sur_buf = nullptr;
+  int* sur_cnt = nullptr;
+  int sur_tiles = 0;
   double quiet_k = 0.0;   // rate bound of the chemistry's cold-gas shortcut (set with prm)
   // asynchronous budget read: pinned landing area [acc3, stored, timeout word], event, and the
   // host-side terms as of the request
@@ -372,6 +376,8 @@ static int enqueue_step(aton_handle h, cudaStream_t s) {
       a.sur.norm = mlp_norm(h->sur);
       a.sur.gate = (float)h->sur_p.gate_substeps;
       a.sur.resid = (float)h->sur_p.residual_max;
+      a.sur.buf = h->sur_buf;
+      a.sur.cnt = h->sur_cnt;
       e = launch_fused_tma(h->ty, a, h->tma[ti], s);
     } else if (h->mode == ATON_MODE_FUSED && h->tma_ok[ti]) {
       e = launch_fused_tma(h->ty, a, h->tma[ti], s);
@@ -409,10 +415,30 @@ static int enqueue_step(aton_handle h, cudaStream_t s) {
   return ATON_OK;
 }
 
+// The fused kernel's per-tile surrogate lists for the current tiling (counts zeroed; the kernel
+// leaves them zero). Captured graphs hold the pointers, so they are dropped on a reallocation.
+static int ensure_sur_lists(aton_handle h) {
+  const int need = fused_tiles(h->nx, h->ny, h->nz, h->ty, h->tz);
+  if (h->sur_tiles >= need) return ATON_OK;
+  CU(cudaStreamSynchronize(h->stream()));
+  cudaFree(h->sur_buf); cudaFree(h->sur_cnt);
+  h->sur_buf = nullptr; h->sur_cnt = nullptr; h->sur_tiles = 0;
+  drop_graphs(h);
+  CU(cudaMalloc(&h->sur_buf, sizeof(SurRec) * kSurCap * (size_t)need));
+  CU(cudaMalloc(&h->sur_cnt, sizeof(int) * (size_t)need));
+  CU(cudaMemsetAsync(h->sur_cnt, 0, sizeof(int) * (size_t)need, h->stream()));
+  h->sur_tiles = need;
+  return ATON_OK;
+}
+
 static int prepare(aton_handle h) {
   if (!h->fields_set) return fail(ATON_ERR_STATE, "aton_set_fields has not been called");
   int rc = ensure_slots(h);
   if (rc) return rc;
+  if (sur_on(h) && !plain_only(h) && h->mode == ATON_MODE_FUSED) {
+    rc = ensure_sur_lists(h);
+    if (rc) return rc;
+  }
   if (h->tiles_dirty) {
     rc = upload_sources(h);
     if (rc) return rc;
@@ -616,6 +642,7 @@ void aton_finalize(aton_handle h) {
   free_slots(h->slots);
   cudaFree(h->d_srcbuf);
   cudaFree(h->sur_list); cudaFree(h->sur_count);
+  cudaFree(h->sur_buf); cudaFree(h->sur_cnt);
   cudaFree(h->st_edges); cudaFree(h->st_part); cudaFree(h->st_out); cudaFree(h->st_u64);
   if (h->bud_pin) cudaFreeHost(h->bud_pin);
   for (int b = 0; b < 2; ++b) {

@@ -52,12 +52,21 @@ struct Fields {
   float* Fz;
 };
 
+// A cell the fused kernel's surrogate gate selected, kept until the end of its CTA (F as F / c).
+struct SurRec {
+  float N, X, Y, Z, y, T, n;
+  int o;
+};
+constexpr int kSurCap = 64;   // cells per CTA; a cell beyond them takes the exact operator at once
+
 // The chemistry surrogate in the fused kernel (surrogate instance only).
 struct SurList {
   const MlpImage* img = nullptr;   // BF16 weight image of the network (device)
   const MlpNorm* norm = nullptr;   // normalisation and training range (device)
   float gate = 0.f;                // sub-step estimate at which a cell is offered
   float resid = 0.f;               // photon residual up to which a prediction is accepted
+  SurRec* buf = nullptr;           // [tile][kSurCap] selected cells (device)
+  int* cnt = nullptr;              // [tile] cells listed (zero between steps)
 };
 
 struct FusedArgs {

@@ -326,15 +326,9 @@ __device__ __forceinline__ bool sur_warp(const StepParams& P, const SurList& S, 
   return cand && sur_accept(P, nm, S.resid, o, n, N, y, T, N1, y1, T1);
 }
 
-// A cell the fused kernel's surrogate gate selected, kept in shared memory until the end of the
-// CTA's z-loop (F as F / c).
-struct SurRec {
-  float N, X, Y, Z, y, T, n;
-  int o;
-};
-constexpr int kSurCap = 64;   // cells per CTA; a cell beyond them takes the exact operator at once
-
-// The fused kernel's deferral (the chem_cell hook): a candidate goes to the CTA's list.
+// The fused kernel's deferral (the chem_cell hook): a candidate goes to the CTA's list, a region
+// of device memory of its own (global atomics on a rare path: shared-memory atomics in the plane
+// loop would tie the compiler's hands on the ring accesses, which measured 12 % slower).
 struct SurDefer {
   const StepParams& P;
   const SurList& S;
@@ -354,7 +348,7 @@ struct SurDefer {
 // Chemistry of the transported cell, its tallies and the store of the new state (physical F:
 // the chemistry scales F / c by its photon ratio times c). With `sur` set the cell takes the
 // network's accepted prediction (N1, y1, T1; F scaled with N) instead of the exact operator.
-// With a deferral `defer` (SurDefer) a selected cell is listed and neither stored nor tallied.
+// With a deferral `defer` (SurDefer) a selected cell is listed (and overwritten later).
 template <bool STD, class Defer = NoDefer>
 __device__ __forceinline__ void chem_tally_store(const StepParams& P, Tally& tl, float cn, float4 u,
                                                  float cy, float cT, const Fields& out, float* Yf,
@@ -369,8 +363,10 @@ __device__ __forceinline__ void chem_tally_store(const StepParams& P, Tally& tl,
     Nn = N1; Xn *= fr; Yn *= fr; Zn *= fr; cy = y1; cT = T1;
     tl.sur += 1;
   } else {
+    // (a deferred cell comes back untouched, F still as F / c, with no sub-steps: it is stored
+    // and tallied like that -- no absorption -- and its CTA's surrogate pass overwrites it; an
+    // early return here made every store and tally conditional and cost 12 % of the step)
     co = chem_cell<STD>(P, cn, Nn, Xn, Yn, Zn, cy, cT, P.c, defer);
-    if (co.deferred) return;
   }
   tl.absorbed.add(N0 - Nn);
   tl.sub += co.nsub;
@@ -390,11 +386,11 @@ __device__ __forceinline__ void chem_tally_store(const StepParams& P, Tally& tl,
 constexpr int kSurScratchBytes = 2 * 2 * 16 * kP2 * 2;
 template <bool STD>
 __device__ __forceinline__ void sur_tail(const StepParams& P, const SurList& S, const SurRec* buf,
-                                         const int* cnt, Tally& tl, const Fields& out, float* Yf,
+                                         int* cnt, Tally& tl, const Fields& out, float* Yf,
                                          float* Tf, void* scratch) {
   static_assert(kSurCap <= 64, "two warps run the list");
-  __syncthreads();
-  const int nc = min(*cnt, kSurCap);
+  __syncthreads();   // (orders the list's writes, global memory included, before its reads)
+  const int nc = min(*reinterpret_cast<volatile int*>(cnt), kSurCap);
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int w = tid >> 5, lane = tid & 31;
   if (w < 2 && w * 32 < nc) {   // (uniform within the warp)
@@ -408,6 +404,10 @@ __device__ __forceinline__ void sur_tail(const StepParams& P, const SurList& S, 
     if (valid)
       chem_tally_store<STD>(P, tl, r.n, make_float4(r.N, r.X, r.Y, r.Z), r.y, r.T, out, Yf, Tf,
                             r.o, acc, N1, y1, T1);
+  }
+  if (nc > 0) {   // the next step's list starts empty (every thread has read the count)
+    __syncthreads();
+    if (tid == 0) *cnt = 0;
   }
 }
 

@@ -107,8 +107,8 @@ struct Layout {
 // cell and no own slot needs patching; the bounds tests fold away. HLL: the HLL intercell flux
 // instead of global Lax-Friedrichs (the ring then also holds each cell's speed bounds). SUR:
 // the chemistry surrogate; a cell the gate selects (off the one-sub-step shortcut) is listed in
-// shared memory and, after the z-loop, runs through the network (sur_tail), the accepted
-// predictions replacing the exact operator.
+// the CTA's region of a device buffer and, after the z-loop, runs through the network (sur_tail),
+// the accepted predictions replacing the exact operator.
 template <int TY, bool PER, bool STD, bool FULL, bool HLL = false, bool SUR = false>
 __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
                                                            const __grid_constant__ TmaMaps M) {
@@ -153,11 +153,8 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
     if (!failed && !mbar_wait(&full[k % kStages], (k / kStages) & 1)) failed = true;
   };
 
-  __shared__ SurRec s_sur[SUR ? kSurCap : 1];   // the CTA's surrogate list
-  __shared__ int s_nsur;
   int issued = 0;   // planes issued so far (thread 0)
   if (tid == 0) {
-    if (SUR) s_nsur = 0;
     for (int s = 0; s < kStages; ++s) mbar_init(&full[s], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     for (; issued < kStages && issued < nplanes; ++issued) issue(issued);
@@ -282,7 +279,8 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
       }
       if (SUR)
         chem_tally_store<STD>(P, tl, cn, u, cy, cT, A.out, A.y, A.T, o, false, 0.f, 0.f, 0.f,
-                              SurDefer{P, A.sur, s_sur, &s_nsur, (int)o});
+                              SurDefer{P, A.sur, A.sur.buf + (size_t)tile * kSurCap,
+                                       A.sur.cnt + tile, (int)o});
       else
         chem_tally_store<STD>(P, tl, cn, u, cy, cT, A.out, A.y, A.T, o);
     }
@@ -300,7 +298,8 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
       mbar_wait(&full[k % kStages], (k / kStages) & 1);
   if (SUR) {
     static_assert(!SUR || L::RING_BYTES >= kSurScratchBytes, "ring too small for the network");
-    sur_tail<STD>(P, A.sur, s_sur, &s_nsur, tl, A.out, A.y, A.T, RU);
+    sur_tail<STD>(P, A.sur, A.sur.buf + (size_t)tile * kSurCap, A.sur.cnt + tile, tl, A.out,
+                  A.y, A.T, RU);
   }
   flush_tally<TY>(tl, A.slots, tile);
 }
