@@ -161,6 +161,47 @@ __device__ __forceinline__ void m1_axis_speeds(const M1Speeds& m, float gd, floa
   hi = 0.5f * (b + r);
 }
 
+// The closure pair of m1_iso_w and the HLL wave-speed bounds (lo, hi) of m1_speeds /
+// m1_axis_speeds along the axes in the mask AX (bit 0 x, bit 1 y, bit 2 z) in one pass: the
+// reciprocal of N, f^2, s = sqrt(4 - 3 f^2) and 1/(5 + 2 s) serve both (the fused HLL kernel
+// evaluates it for every ring slot; a halo slot needs the speeds along one axis only). An empty
+// cell (N <= kNTiny) takes the isotropic pair and the speeds of f = 0, +-1/sqrt(3).
+template <int AX>
+__device__ __forceinline__ float2 m1_iso_w_speeds(float N, float fx, float fy, float fz,
+                                                  float2* sx, float2* sy, float2* sz) {
+  const bool rad = N > kNTiny;
+  const float rN = rcp_fast(rad ? N : 1.f);   // N in (1e-30, 8e37): the reciprocal stays normal
+  float gx = fx * rN, gy = fy * rN, gz = fz * rN;
+  const float f2r = gx * gx + gy * gy + gz * gz;
+  const bool over = f2r > 1.f;
+  const float k = over ? rN * rcp_fast(f2r) : rN;   // f2 in (1, 3e38]: a normal reciprocal
+  const float f2 = rad ? fminf(f2r, 1.f) : 0.f;
+  const float s = sqrtf(4.f - 3.f * f2);        // in [1, 2]
+  const float r5 = rcp_fast(5.f + 2.f * s);
+  const float r2 = rcp_fast(2.f + s);
+  const float iso = (1.f + s - 2.f * f2) * (r5 * N);
+  const float w = fmaf(3.f, r2, 6.f) * r5 * k;
+  // speeds: g on the unit sphere where |g| > 1, zero for an empty cell
+  const float gs = rad ? (over ? rsqrtf(f2r) : 1.f) : 0.f;
+  gx *= gs; gy *= gs; gz *= gs;
+  const float chi = (3.f + 4.f * f2) * r5;
+  const float dcf = fmaf(6.f * (3.f + 4.f * f2), rcp_fast(s), 8.f * (5.f + 2.f * s)) * r5 * r5;
+  const float P1 = f2 * fmaf(6.f, r2, 12.f) * r5 * dcf - 2.f;   // (3 chi - 1) chi'/f - 2
+  const float rf2 = f2 > 1e-30f ? rcp_fast(f2) : 0.f;          // f2 in (1e-30, 1]
+  auto axis = [&](float gd) {
+    const float mu2 = fminf(gd * gd * rf2, 1.f);
+    const float C = (1.f - mu2) * P1 + 2.f * chi * (1.f - 3.f * mu2) +
+                    2.f * dcf * f2 * (3.f * mu2 - 1.f);
+    const float b = dcf * gd;
+    const float r = sqrtf(fmaxf(b * b - C, 0.f));
+    return make_float2(0.5f * (b - r), 0.5f * (b + r));
+  };
+  if (AX & 1) *sx = axis(gx);
+  if (AX & 2) *sy = axis(gy);
+  if (AX & 4) *sz = axis(gz);
+  return rad ? make_float2(iso, w) : make_float2(N > 0.f ? N * (1.f / 3.f) : 0.f, 0.f);
+}
+
 // ---------------------------------------------------------------------------------------
 // Rate fits (the paper defers to Anninos et al. 1997 and Cen 1992; section 2.2). Hui & Gnedin
 // (1997) fits in lambda = 2 T_HI / T, evaluated in log2 form, plus Cen (1992) collisional

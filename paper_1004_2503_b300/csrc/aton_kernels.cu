@@ -254,19 +254,14 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain_transport(const PlainAr
         m1_axis_speeds(mc, gc, lc, hc);
         m1_axis_speeds(ma, ga, la, ha);
         m1_axis_speeds(mb, gb, lb, hb);
-        const float lmp = fminf(0.f, fminf(lc, la)), lpp = fmaxf(0.f, fmaxf(hc, ha));   // face +
-        const float lmm = fminf(0.f, fminf(lb, lc)), lpm = fmaxf(0.f, fmaxf(hb, hc));   // face -
-        // l+ - l- >= 1/sqrt(3) unless both cells stream at f = 1 parallel to the face, where
-        // the two fluxes vanish: the guard then takes their mean
-        const float dp = lpp - lmp, dm = lpm - lmm;
+        // face + between the centre and a, face - between b and the centre (hll_coef: l+ - l-
+        // >= 1/sqrt(3) unless both cells stream at f = 1 parallel to the face, where the two
+        // fluxes vanish and their mean is taken)
+        const HllCoef kp = hll_coef(fminf(0.f, fminf(lc, la)), fmaxf(0.f, fmaxf(hc, ha)));
+        const HllCoef km = hll_coef(fminf(0.f, fminf(lb, lc)), fmaxf(0.f, fmaxf(hb, hc)));
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float Fp = dp > 1e-6f ? hll_face(lmp, lpp, rcp_fast(dp), fc[q], fa[q], u[q], a[q])
-                                      : 0.5f * (fc[q] + fa[q]);
-          const float Fm = dm > 1e-6f ? hll_face(lmm, lpm, rcp_fast(dm), fb[q], fc[q], b[q], u[q])
-                                      : 0.5f * (fb[q] + fc[q]);
-          acc[q] += Fp - Fm;
-        }
+        for (int q = 0; q < 4; ++q)
+          acc[q] += hll_face(kp, fc[q], fa[q], u[q], a[q]) - hll_face(km, fb[q], fc[q], b[q], u[q]);
       }
     }
     // acc is the sum over the three axes of (flux at the high face - flux at the low face)

@@ -10,7 +10,9 @@
 //    per-CTA slot, then summed over the slots in index order;
 //  - the per-density-bin sums of y and N: within each group of 32 consecutive cells (a warp),
 //    runs of equal density bin are summed in FP32 by a segmented tree, and each run's sum is
-//    added in FP64 to the warp's own row of bins (runs of the same bin in lane order).
+//    added with an error-free TwoSum to the warp's own row of FP32 (sum, error) pairs (runs of
+//    the same bin in lane order; FP64 arithmetic, a slow pipe on this part, stays out of the
+//    loop), reduced in FP64 at the end.
 // Bin decisions compare the stored floats with float edges prepared on the host (a log2 guess
 // then an exact fix-up), so they are exact and reproducible.
 #include "aton_internal.h"
@@ -35,6 +37,14 @@ __device__ __forceinline__ int find_bin(float v, const float* E, int nb, float g
 
 using Kf = TwoSumF;   // compensated FP32 sum
 
+// (sum, error) pair += v with Knuth's TwoSum (valid whatever the magnitudes)
+__device__ __forceinline__ void pair_add(float2& p, float v) {
+  const float t = p.x + v;
+  const float bp = t - p.x;
+  p.y += (p.x - (t - bp)) + (v - bp);
+  p.x = t;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -47,7 +57,7 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats(const StatsArgs a) {
   __shared__ unsigned int HJ[kMB * kMB];
   __shared__ unsigned int Cn[kMB];
   __shared__ unsigned int Cp;
-  __shared__ double Wb[kWarps][kMB][2];
+  __shared__ float2 Wb[kWarps][kMB][2];   // (sum, error) of y and of N per density bin
   __shared__ double Ws[kWarps][kStatsScalars];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int nb_n = a.nb_n, nb_y = a.nb_y, nb_J = a.nb_J;
@@ -60,7 +70,10 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats(const StatsArgs a) {
   // scalar sums: y, nH, nH y, N, T, nH T, N on the plateau
   Kf sy, sn, sny, sN, sT, snT, sNp;
   unsigned int cp = 0;
-  for (int i = lane; i < kMB; i += 32) { Wb[w][i][0] = 0.0; Wb[w][i][1] = 0.0; }
+  for (int i = lane; i < kMB; i += 32) {
+    Wb[w][i][0] = make_float2(0.f, 0.f);
+    Wb[w][i][1] = make_float2(0.f, 0.f);
+  }
   __syncwarp();
   const long long ncell = a.ncell;
   const long long stride = (long long)gridDim.x * kStatsThreads;
@@ -68,20 +81,24 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats(const StatsArgs a) {
   for (long long base = (long long)blockIdx.x * kStatsThreads + (t & ~31); base < ncell;
        base += stride) {
     const long long i = base + lane;
-    int bn = -1;
+    int bn = -1, ky = 0, kJ = 0;
     float yv = 0.f, Nv = 0.f;
     if (i < ncell) {
       const float n = __ldg(a.nH + i), yy = __ldg(a.y + i), NN = __ldg(a.N + i), TT = __ldg(a.T + i);
       bn = find_bin(n, E[0], nb_n, a.g[0], a.g[1]);
-      const int by = find_bin(yy, E[1], nb_y, a.g[2], a.g[3]);
-      const int bJ = find_bin(NN, E[2], nb_J, a.g[4], a.g[5]);
-      atomicAdd(&Hy[bn * nb_y + by], 1u);
-      atomicAdd(&HJ[bn * nb_J + bJ], 1u);
-      atomicAdd(&Cn[bn], 1u);
+      ky = bn * nb_y + find_bin(yy, E[1], nb_y, a.g[2], a.g[3]);
+      kJ = bn * nb_J + find_bin(NN, E[2], nb_J, a.g[4], a.g[5]);
       sy.add(yy); sn.add(n); sny.add(n * yy); sN.add(NN); sT.add(TT); snT.add(n * TT);
       if (n < a.n_plateau) { sNp.add(NN); ++cp; }
       yv = yy;
       Nv = NN;
+    }
+    // (aggregating the counts over the warp, with match-any rounds or run lengths, measured
+    // slower than the contended shared-memory atomics)
+    if (i < ncell) {
+      atomicAdd(&Hy[ky], 1u);
+      atomicAdd(&HJ[kJ], 1u);
+      atomicAdd(&Cn[bn], 1u);
     }
     // per-density-bin sums: runs of consecutive lanes with the same bin are summed by a
     // segmented tree (lane L adds lane L+o while no run starts in (L, L+o]), then each run's
@@ -100,8 +117,8 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats(const StatsArgs a) {
     unsigned grp = __match_any_sync(full, pending ? bn : -1 - lane);
     while (__any_sync(full, pending)) {
       if (pending && lane == __ffs(grp) - 1) {
-        Wb[w][bn][0] += (double)ry;
-        Wb[w][bn][1] += (double)rN;
+        pair_add(Wb[w][bn][0], ry);
+        pair_add(Wb[w][bn][1], rN);
         pending = false;
       }
       grp &= grp - 1u;
@@ -128,7 +145,7 @@ __global__ void __launch_bounds__(kStatsThreads) k_stats(const StatsArgs a) {
   if (t < 2 * kMB) {
     const int b = t >> 1, q = t & 1;
     double r = 0.0;
-    for (int k = 0; k < kWarps; ++k) r += Wb[k][b][q];
+    for (int k = 0; k < kWarps; ++k) r += (double)Wb[k][b][q].x + (double)Wb[k][b][q].y;
     pb[t] = r;
   }
   for (int i = t; i < nb_n * nb_y; i += kStatsThreads)

@@ -175,6 +175,18 @@ __device__ __forceinline__ void ring_put_speeds(float2* SX, float2* SY, float2* 
   SZ[slot] = make_float2(lo, hi);
 }
 
+// Store the record of a slot with its speed bounds along the axes in AX (the fused HLL kernel:
+// x, y and z for the tile's own slots, only x or only y for a halo column or row); returns the
+// cell's z flux.
+template <int AX>
+__device__ __forceinline__ float4 ring_put_hll(float4* RU, float2* RW, float2* SX, float2* SY,
+                                               float2* SZ, int slot, const float4& u) {
+  const float2 q = m1_iso_w_speeds<AX>(u.x, u.y, u.z, u.w, SX + slot, SY + slot, SZ + slot);
+  RU[slot] = u;
+  RW[slot] = q;
+  return z_flux_q(u, q);
+}
+
 // fluxes along x and y of a state and its closure pair (along z: z_flux_q)
 __device__ __forceinline__ float4 x_flux_q(const float4& u, const float2& q) {
   const float w = __fmul_rn(q.y, u.y);
@@ -185,10 +197,21 @@ __device__ __forceinline__ float4 y_flux_q(const float4& u, const float2& q) {
   return make_float4(u.z, __fmul_rn(w, u.y), fmaf(w, u.z, q.x), __fmul_rn(w, u.w));
 }
 
-// HLL face flux of one component: (l+ Phi_L - l- Phi_R + l+ l- (u_R - u_L)) / (l+ - l-)
-__device__ __forceinline__ float hll_face(float lm, float lp, float rd, float PL, float PR,
-                                          float uL, float uR) {
-  return (lp * PL - lm * PR + lp * lm * (uR - uL)) * rd;
+// Coefficients of the HLL face flux F = a Phi_L + b Phi_R + c (u_R - u_L) for the bounds
+// l- <= 0 <= l+ of a face: a = l+ / (l+ - l-), b = -l- / (l+ - l-), c = l+ l- / (l+ - l-); where
+// l+ - l- vanishes (both cells streaming at f = 1 parallel to the face, whose fluxes then vanish
+// too) the mean, a = b = 1/2, c = 0. Taken once per face, so a component costs three operations.
+struct HllCoef {
+  float a, b, c;
+};
+__device__ __forceinline__ HllCoef hll_coef(float lm, float lp) {
+  const float d = lp - lm;
+  const bool g = d > 1e-6f;
+  const float r = rcp_fast(g ? d : 1.f);   // d <= 2
+  return g ? HllCoef{lp * r, -lm * r, lp * lm * r} : HllCoef{0.5f, 0.5f, 0.f};
+}
+__device__ __forceinline__ float hll_face(const HllCoef& k, float PL, float PR, float uL, float uR) {
+  return fmaf(k.c, uR - uL, fmaf(k.a, PL, k.b * PR));
 }
 
 // (flux through the high face) - (flux through the low face) along one axis, for the centre c
@@ -196,19 +219,12 @@ __device__ __forceinline__ float hll_face(float lm, float lp, float rd, float PL
 __device__ __forceinline__ float4 hll_axis(const float4& fl, const float4& fc, const float4& fh,
                                            const float4& ul, const float4& uc, const float4& uh,
                                            const float2& sl, const float2& sc, const float2& sh) {
-  const float lmp = fminf(0.f, fminf(sc.x, sh.x)), lpp = fmaxf(0.f, fmaxf(sc.y, sh.y));
-  const float lmm = fminf(0.f, fminf(sl.x, sc.x)), lpm = fmaxf(0.f, fmaxf(sl.y, sc.y));
-  const float dp = lpp - lmp, dm = lpm - lmm;
-  const bool gp = dp > 1e-6f, gm = dm > 1e-6f;
-  const float rp = rcp_fast(gp ? dp : 1.f), rm = rcp_fast(gm ? dm : 1.f);   // dp, dm <= 2
-  auto face = [&](bool g, float lm, float lp, float rd, float PL, float PR, float uL, float uR) {
-    return g ? hll_face(lm, lp, rd, PL, PR, uL, uR) : 0.5f * (PL + PR);
-  };
-  return make_float4(
-      face(gp, lmp, lpp, rp, fc.x, fh.x, uc.x, uh.x) - face(gm, lmm, lpm, rm, fl.x, fc.x, ul.x, uc.x),
-      face(gp, lmp, lpp, rp, fc.y, fh.y, uc.y, uh.y) - face(gm, lmm, lpm, rm, fl.y, fc.y, ul.y, uc.y),
-      face(gp, lmp, lpp, rp, fc.z, fh.z, uc.z, uh.z) - face(gm, lmm, lpm, rm, fl.z, fc.z, ul.z, uc.z),
-      face(gp, lmp, lpp, rp, fc.w, fh.w, uc.w, uh.w) - face(gm, lmm, lpm, rm, fl.w, fc.w, ul.w, uc.w));
+  const HllCoef kp = hll_coef(fminf(0.f, fminf(sc.x, sh.x)), fmaxf(0.f, fmaxf(sc.y, sh.y)));
+  const HllCoef km = hll_coef(fminf(0.f, fminf(sl.x, sc.x)), fmaxf(0.f, fmaxf(sl.y, sc.y)));
+  return make_float4(hll_face(kp, fc.x, fh.x, uc.x, uh.x) - hll_face(km, fl.x, fc.x, ul.x, uc.x),
+                     hll_face(kp, fc.y, fh.y, uc.y, uh.y) - hll_face(km, fl.y, fc.y, ul.y, uc.y),
+                     hll_face(kp, fc.z, fh.z, uc.z, uh.z) - hll_face(km, fl.z, fc.z, ul.z, uc.z),
+                     hll_face(kp, fc.w, fh.w, uc.w, uh.w) - hll_face(km, fl.w, fc.w, ul.w, uc.w));
 }
 
 // HLL update of the centre cell: u' = u - lam sum_d (F_{d,+} - F_{d,-}). U, W, SX, SY point at

@@ -200,10 +200,27 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
     }
     return u;
   };
-  // the prepared slot into ring plane r; returns the z flux (Fz/c, Dxz, Dyz, Dzz) N
+  // the prepared own slot into ring plane r; returns the z flux (Fz/c, Dxz, Dyz, Dzz) N
   auto put = [&](int r, int rslot, const float4& u) {
-    if (HLL) ring_put_speeds(SX + r * L::PLR, SY + r * L::PLR, SZ + r * L::PLR, rslot, u);
+    if (HLL)
+      return ring_put_hll<7>(RU + r * L::PLR, RW + r * L::PLR, SX + r * L::PLR, SY + r * L::PLR,
+                             SZ + r * L::PLR, rslot, u);
     return ring_put(RU + r * L::PLR, RW + r * L::PLR, rslot, u);
+  };
+  // the prepared halo slot: with HLL a halo row needs its speeds along y only, a halo column
+  // along x only (warps 0 and 1 hold the rows, warp 2 the columns: no divergence)
+  const bool hrow = hy < 0 || hy >= TY;
+  auto put_halo = [&](int r, const float4& u) {
+    if (HLL) {
+      float4* U = RU + r * L::PLR;
+      float2* W = RW + r * L::PLR;
+      if (hrow)
+        ring_put_hll<2>(U, W, SX + r * L::PLR, SY + r * L::PLR, SZ + r * L::PLR, hrslot, u);
+      else
+        ring_put_hll<1>(U, W, SX + r * L::PLR, SY + r * L::PLR, SZ + r * L::PLR, hrslot, u);
+    } else {
+      ring_put(RU + r * L::PLR, RW + r * L::PLR, hrslot, u);
+    }
   };
 
   // plane z0-1 (own slot only) into ring plane 0, plane z0 into ring plane 1
@@ -214,7 +231,7 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
     const float* st = stage0 + (1 % kStages) * L::STAGE;
     const int p = plane_of(z0);
     put(1, orslot, prep(st, oslot, own_out, ocol, p));
-    if (hslot >= 0) put(1, hrslot, prep(st, hslot, halo_out, hcol, p));
+    if (hslot >= 0) put_halo(1, prep(st, hslot, halo_out, hcol, p));
   }
   int sp = A.tsrc_start[tile];
   const int se = A.tsrc_start[tile + 1];
@@ -237,7 +254,7 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
       const int p = plane_of(z + 1);
       up = prep(st, oslot, own_out, ocol, p);
       pp = put(rkn, orslot, up);
-      if (hslot >= 0) put(rkn, hrslot, prep(st, hslot, halo_out, hcol, p));
+      if (hslot >= 0) put_halo(rkn, prep(st, hslot, halo_out, hcol, p));
     }
     // chemistry fields of the own cell, one plane ahead
     float ny_ = 0.f, nT_ = 1.f, nn_ = 1.f;
@@ -327,6 +344,14 @@ cudaError_t set_tma_attr() {
   e = cudaFuncSetAttribute(k_fused_tma<TY, PER, true, true, false, true>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Layout<TY>::BYTES);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_fused_tma<TY, PER, true, false, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)Layout<TY, true>::BYTES);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_fused_tma<TY, PER, true, true, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)Layout<TY, true>::BYTES);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_fused_tma<TY, PER, false, false, true>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)Layout<TY, true>::BYTES);
@@ -337,9 +362,14 @@ cudaError_t launch_tma_t(const FusedArgs& a, const TmaMaps& m, cudaStream_t s) {
   dim3 grid((a.P.nx + kTileX - 1) / kTileX, (a.P.ny + TY - 1) / TY, (a.P.nz + a.tz - 1) / a.tz);
   dim3 block(kTileX, TY);
   const bool full = a.P.nx % kTileX == 0 && a.P.ny % TY == 0;
-  if (a.P.hll)
-    k_fused_tma<TY, PER, false, false, true><<<grid, block, Layout<TY, true>::BYTES, s>>>(a, m);
-  else if (a.sur.img) {   // the surrogate instances
+  if (a.P.hll) {   // (the standard-chemistry and full-tile instances as for GLF)
+    if (!standard_chemistry(a.P))
+      k_fused_tma<TY, PER, false, false, true><<<grid, block, Layout<TY, true>::BYTES, s>>>(a, m);
+    else if (full)
+      k_fused_tma<TY, PER, true, true, true><<<grid, block, Layout<TY, true>::BYTES, s>>>(a, m);
+    else
+      k_fused_tma<TY, PER, true, false, true><<<grid, block, Layout<TY, true>::BYTES, s>>>(a, m);
+  } else if (a.sur.img) {   // the surrogate instances
     if (!standard_chemistry(a.P))
       k_fused_tma<TY, PER, false, false, false, true><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);
     else if (full)
