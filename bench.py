@@ -40,6 +40,9 @@ NCU_TRAFFIC = {
     # k_fused_tma, tile 32x4x64, lognormal 256^3: dram__bytes_read.sum 486.51 MB +
     # dram__bytes_write.sum 362.43 MB per launch over 16,777,216 cells
     "39f8acbedd89": (486.513920e6 + 362.430208e6) / 16777216,
+    # the same kernel with the surrogate hook and instances added (the exact instance's fields
+    # bitwise unchanged): 486.89 MB + 362.55 MB
+    "ac0f3ed55d18": (486.887168e6 + 362.554368e6) / 16777216,
 }
 
 
@@ -298,7 +301,8 @@ def ours(args, world, rank, local):
     def maxtime(t):
         return replica_time(t, dist, "cuda")
 
-    a = A.from_workload(st, idx, rate, run)
+    flux = {"glf": A.FLUX_GLF, "hll": A.FLUX_HLL}[args.flux]
+    a = A.from_workload(st, idx, rate, run, flux=flux)
     a.set_stream(stream)
     if args.tile:
         ty, tz = (int(v) for v in args.tile.split(","))
@@ -398,7 +402,7 @@ def ours(args, world, rank, local):
             for k in ("N", "Fx", "Fy", "Fz", "y", "T")}
     b = A.Aton(run["nx"], run["ny"], run["nz"], run["dx"], run["c"], run["dt"])
     b.set_params(bc=A.BC_PERIODIC, sigma_n=run["sigma_n"], sigma_e=run["sigma_e"],
-                 e_gamma_eV=run["e_gamma_eV"])
+                 e_gamma_eV=run["e_gamma_eV"], flux=flux)
     b.set_tile(ty, tz)
     b.set_exec(fused_mode, args.graph_batch)
     b.set_fields(pin["N"], pin["Fx"], pin["Fy"], pin["Fz"], pin["T"], pin["nH"], y=ypin)
@@ -445,7 +449,8 @@ def finish(args, world, rank, dist, st, idx, rate, run, desc, ncell, value, ms, 
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "grid": args.grid, "cells": ncell, "sources": len(idx),
-                   "mode": kernel, "graph_batch": args.graph_batch, "tile_ty_tz": [ty, tz],
+                   "mode": kernel, "flux": args.flux, "graph_batch": args.graph_batch,
+                   "tile_ty_tz": [ty, tz],
                    "autotune_ms_per_step": tune_ms, "parallelism": f"replicas x{world}",
                    "l2": f"no flush: {44 * ncell / 1e9:.1f} GB of state per step >> 126 MB L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -496,6 +501,8 @@ def main():
     ap.add_argument("--no-unfused", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--tile", default="", help="TY,TZ of the fused kernel (skips the autotuner)")
+    ap.add_argument("--flux", default="glf", choices=["glf", "hll"],
+                    help="intercell flux: global Lax-Friedrichs (the paper's) or HLL")
     ap.add_argument("--kernel", default="tma", choices=["tma", "ldg"],
                     help="fused kernel used with --tile (the autotuner chooses otherwise)")
     args = ap.parse_args()
