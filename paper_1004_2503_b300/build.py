@@ -14,8 +14,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libaton.so")
-SOURCES = ["aton_capi.cu", "aton_kernels.cu", "aton_tma.cu", "aton_mlp.cu", "aton_static.cu",
-           "aton_stats.cu", "aton_sources.cu"]
+SOURCES = ["aton_capi.cu", "aton_kernels.cu", "aton_tma.cu", "aton_mlp.cu", "aton_mlp_tc.cu",
+           "aton_static.cu", "aton_stats.cu", "aton_sources.cu"]
 HEADERS = ["aton_device.cuh", "aton_internal.h", "aton_step_common.cuh", "aton_mlp.cuh",
            "aton_stats.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -111,6 +111,12 @@ inline bool standard_chemistry(const StepParams& P) {
   return !P.fixed_T && P.cooling && P.coll_ion && !(P.clR_A > 0.f) && !(P.clI_A > 0.f);
 }
 
+// ---- training step of the surrogate MLP on tcgen05 (aton_mlp_tc.cu) ----
+__global__ void k_mlp_train_tc(const MlpImage* __restrict__ img, const float* __restrict__ X,
+                               const float* __restrict__ T, int n, float inv_count, float* partial,
+                               float* loss_part, unsigned int* err);
+size_t mlp_train_tc_smem();
+
 // ---- last-failure message of the calling thread (aton_capi.cu) ----
 void set_last_message(const char* msg);
 

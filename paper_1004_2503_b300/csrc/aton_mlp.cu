@@ -7,10 +7,9 @@
 // operator (the plain step's chemistry kernel writes them through a pair sink).
 //
 // Kernels:
-//   k_mlp_train   -- forward and backward of 128 rows per CTA on BF16 tensor cores (mma.sync
-//                    m16n8k16, FP32 accumulation); the weight gradients are tensor-core products
-//                    over the CTA's rows of transposed BF16 copies held in shared memory; one FP32
-//                    partial gradient per CTA (summed later in a fixed order: deterministic).
+//   k_mlp_train_tc -- (aton_mlp_tc.cu) forward and backward of 128 rows per CTA on the tcgen05
+//                    tensor cores, accumulators in tensor memory; one FP32 partial gradient per
+//                    CTA (summed later in a fixed order: deterministic).
 //   k_mlp_adam    -- sums the partials, Adam update of the FP32 master weights, refreshes the
 //                    BF16 weight image.
 //   k_mlp_forward -- inference (normalised features -> normalised outputs).
@@ -33,22 +32,9 @@ namespace aton {
 
 namespace {
 
-constexpr int kRows = 128;          // rows per training CTA (8 warps x 16)
-constexpr int kTP = kRows + 8;      // row pitch of the transposed activation copies
+constexpr int kRows = 128;          // rows per CTA (training: one per thread; inference: 8 x 16)
 constexpr int kThreads = 256;
 constexpr int kRecLen = 8;          // pair record: nH, N, y, T, N', y', T', sub-steps
-
-struct TrainSmem {
-  MlpImage W;
-  __nv_bfloat16 XT[16 * kTP];       // [input][row]
-  __nv_bfloat16 H1T[kMlpH * kTP];   // [unit][row]
-  __nv_bfloat16 H2T[kMlpH * kTP];
-  __nv_bfloat16 D1T[kMlpH * kTP];   // dL/dz1, [unit][row]
-  __nv_bfloat16 D2T[kMlpH * kTP];
-  __nv_bfloat16 DYT[16 * kTP];      // dL/dy, [output][row] (rows 8..15 stay zero)
-  float db1[8][kMlpH], db2[8][kMlpH], db3[8][8];
-  float loss[8];
-};
 
 __device__ __forceinline__ void copy_image(MlpImage* dst, const MlpImage* src, bool full) {
   const size_t nbytes = full ? sizeof(MlpImage) : offsetof(MlpImage, W2T);
@@ -59,217 +45,6 @@ __device__ __forceinline__ void copy_image(MlpImage* dst, const MlpImage* src, b
     const float* sb = src->b1;
     float* db = dst->b1;
     for (int i = threadIdx.x; i < 2 * kMlpH + 8; i += blockDim.x) db[i] = sb[i];
-  }
-}
-
-// A fragment of rows r0..r0+15, k0..k0+15 from a transposed [m][k] array (pitch kTP)
-__device__ __forceinline__ void frag_a_T(const __nv_bfloat16* AT, int m0, int k0, unsigned a[4]) {
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  a[0] = ld_pair(AT + (m0 + g) * kTP + k0 + 2 * t);
-  a[1] = ld_pair(AT + (m0 + g + 8) * kTP + k0 + 2 * t);
-  a[2] = ld_pair(AT + (m0 + g) * kTP + k0 + 2 * t + 8);
-  a[3] = ld_pair(AT + (m0 + g + 8) * kTP + k0 + 2 * t + 8);
-}
-
-// sum over the 8 lanes that share t (lanes g = 0..7): result valid in lanes with g == 0
-__device__ __forceinline__ float sum_over_g(float v) {
-  v += __shfl_xor_sync(0xffffffffu, v, 4);
-  v += __shfl_xor_sync(0xffffffffu, v, 8);
-  v += __shfl_xor_sync(0xffffffffu, v, 16);
-  return v;
-}
-
-__global__ void __launch_bounds__(kThreads) k_mlp_train(const MlpImage* __restrict__ img,
-                                                        const float* __restrict__ X,
-                                                        const float* __restrict__ T, int n,
-                                                        float inv_count, float* partial,
-                                                        float* loss_part) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  TrainSmem& S = *reinterpret_cast<TrainSmem*>(smraw);
-  copy_image(&S.W, img, true);
-  // zero the padded rows of XT (inputs 5..15) and DYT (outputs 3..15)
-  for (int i = threadIdx.x; i < 16 * kTP; i += kThreads) {
-    S.XT[i] = __float2bfloat16(0.f);
-    S.DYT[i] = __float2bfloat16(0.f);
-  }
-  __syncthreads();
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int rl0 = w * 16;                       // first row of the warp inside the CTA
-  const int rg0 = blockIdx.x * kRows + rl0;     // first global row
-  const int ra = rg0 + g, rb = rg0 + g + 8;
-  const bool va = ra < n, vb = rb < n;
-  // input fragment (features 5..7 and 8..15 are zero)
-  float xa0 = 0.f, xa1 = 0.f, xb0 = 0.f, xb1 = 0.f;
-  if (2 * t < kMlpIn) {
-    if (va) xa0 = X[(size_t)ra * kMlpIn + 2 * t];
-    if (vb) xb0 = X[(size_t)rb * kMlpIn + 2 * t];
-  }
-  if (2 * t + 1 < kMlpIn) {
-    if (va) xa1 = X[(size_t)ra * kMlpIn + 2 * t + 1];
-    if (vb) xb1 = X[(size_t)rb * kMlpIn + 2 * t + 1];
-  }
-  const unsigned xa[4] = {pack_bf16(xa0, xa1), pack_bf16(xb0, xb1), 0u, 0u};
-  S.XT[(2 * t) * kTP + rl0 + g] = __float2bfloat16(xa0);
-  S.XT[(2 * t + 1) * kTP + rl0 + g] = __float2bfloat16(xa1);
-  S.XT[(2 * t) * kTP + rl0 + g + 8] = __float2bfloat16(xb0);
-  S.XT[(2 * t + 1) * kTP + rl0 + g + 8] = __float2bfloat16(xb1);
-
-  float z1[8][4], z2[8][4], y[4];
-  mlp_forward16<true>(S.W, xa, z1, z2, y);
-
-  // dL/dy = 2 (y - target) / (rows * 3) on the three used outputs
-  float dy[4] = {0.f, 0.f, 0.f, 0.f}, sq = 0.f;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int col = 2 * t + (q & 1);
-    const bool v = (q < 2 ? va : vb) && col < kMlpOut;
-    if (v) {
-      const float tg = T[(size_t)(q < 2 ? ra : rb) * kMlpOut + col];
-      const float d = y[q] - tg;
-      dy[q] = 2.f * d * inv_count;
-      sq += d * d;
-    }
-  }
-  // loss and db3 partials
-  sq += __shfl_xor_sync(0xffffffffu, sq, 1);
-  sq += __shfl_xor_sync(0xffffffffu, sq, 2);
-  sq = sum_over_g(sq);
-  if (lane == 0) S.loss[w] = sq;
-  {
-    const float s0 = sum_over_g(dy[0] + dy[2]), s1 = sum_over_g(dy[1] + dy[3]);
-    if (g == 0) { S.db3[w][2 * t] = s0; S.db3[w][2 * t + 1] = s1; }
-  }
-  // transposed copies: dy, h1, h2
-  S.DYT[(2 * t) * kTP + rl0 + g] = __float2bfloat16(dy[0]);
-  S.DYT[(2 * t + 1) * kTP + rl0 + g] = __float2bfloat16(dy[1]);
-  S.DYT[(2 * t) * kTP + rl0 + g + 8] = __float2bfloat16(dy[2]);
-  S.DYT[(2 * t + 1) * kTP + rl0 + g + 8] = __float2bfloat16(dy[3]);
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    const int c = nt * 8 + 2 * t;
-    S.H1T[c * kTP + rl0 + g] = __float2bfloat16(silu(z1[nt][0]));
-    S.H1T[(c + 1) * kTP + rl0 + g] = __float2bfloat16(silu(z1[nt][1]));
-    S.H1T[c * kTP + rl0 + g + 8] = __float2bfloat16(silu(z1[nt][2]));
-    S.H1T[(c + 1) * kTP + rl0 + g + 8] = __float2bfloat16(silu(z1[nt][3]));
-    S.H2T[c * kTP + rl0 + g] = __float2bfloat16(silu(z2[nt][0]));
-    S.H2T[(c + 1) * kTP + rl0 + g] = __float2bfloat16(silu(z2[nt][1]));
-    S.H2T[c * kTP + rl0 + g + 8] = __float2bfloat16(silu(z2[nt][2]));
-    S.H2T[(c + 1) * kTP + rl0 + g + 8] = __float2bfloat16(silu(z2[nt][3]));
-  }
-  // dh2 = dy W3 (K = outputs, padded to 16), dz2 = dh2 * silu'(z2)
-  const unsigned dya[4] = {pack_bf16(dy[0], dy[1]), pack_bf16(dy[2], dy[3]), 0u, 0u};
-  unsigned da[4][4];
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    float c[4] = {0.f, 0.f, 0.f, 0.f};
-    mma_bf16(c, dya, ld_pair(S.W.W3T + (nt * 8 + g) * kP3T + 2 * t), 0u);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) c[q] *= dsilu(z2[nt][q]);
-    const int col = nt * 8 + 2 * t;
-    S.D2T[col * kTP + rl0 + g] = __float2bfloat16(c[0]);
-    S.D2T[(col + 1) * kTP + rl0 + g] = __float2bfloat16(c[1]);
-    S.D2T[col * kTP + rl0 + g + 8] = __float2bfloat16(c[2]);
-    S.D2T[(col + 1) * kTP + rl0 + g + 8] = __float2bfloat16(c[3]);
-    const float s0 = sum_over_g(c[0] + c[2]), s1 = sum_over_g(c[1] + c[3]);
-    if (g == 0) { S.db2[w][col] = s0; S.db2[w][col + 1] = s1; }
-    const int ks = nt >> 1;
-    if ((nt & 1) == 0) { da[ks][0] = pack_bf16(c[0], c[1]); da[ks][1] = pack_bf16(c[2], c[3]); }
-    else { da[ks][2] = pack_bf16(c[0], c[1]); da[ks][3] = pack_bf16(c[2], c[3]); }
-  }
-  // dh1 = dz2 W2, dz1 = dh1 * silu'(z1)
-#pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    float c[4] = {0.f, 0.f, 0.f, 0.f};
-    const __nv_bfloat16* wt = S.W.W2T + (nt * 8 + g) * kP2 + 2 * t;
-#pragma unroll
-    for (int ks = 0; ks < 4; ++ks) mma_bf16(c, da[ks], ld_pair(wt + ks * 16), ld_pair(wt + ks * 16 + 8));
-#pragma unroll
-    for (int q = 0; q < 4; ++q) c[q] *= dsilu(z1[nt][q]);
-    const int col = nt * 8 + 2 * t;
-    S.D1T[col * kTP + rl0 + g] = __float2bfloat16(c[0]);
-    S.D1T[(col + 1) * kTP + rl0 + g] = __float2bfloat16(c[1]);
-    S.D1T[col * kTP + rl0 + g + 8] = __float2bfloat16(c[2]);
-    S.D1T[(col + 1) * kTP + rl0 + g + 8] = __float2bfloat16(c[3]);
-    const float s0 = sum_over_g(c[0] + c[2]), s1 = sum_over_g(c[1] + c[3]);
-    if (g == 0) { S.db1[w][col] = s0; S.db1[w][col + 1] = s1; }
-  }
-  __syncthreads();
-
-  float* P = partial + (size_t)blockIdx.x * kMlpParams;
-  // dW2 = dZ2^T H1 over the CTA's rows: warp w owns out-tile w/2 and in-tiles 4(w%2)..+3
-  {
-    const int m0 = (w >> 1) * 16;
-    float c[4][4] = {};
-    for (int ks = 0; ks < kRows / 16; ++ks) {
-      unsigned a[4];
-      frag_a_T(S.D2T, m0, ks * 16, a);
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int n0 = ((w & 1) * 4 + j) * 8;
-        const __nv_bfloat16* b = S.H1T + (n0 + g) * kTP + ks * 16 + 2 * t;
-        mma_bf16(c[j], a, ld_pair(b), ld_pair(b + 8));
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int n0 = ((w & 1) * 4 + j) * 8 + 2 * t;
-      P[kOffW2 + (m0 + g) * kMlpH + n0] = c[j][0];
-      P[kOffW2 + (m0 + g) * kMlpH + n0 + 1] = c[j][1];
-      P[kOffW2 + (m0 + g + 8) * kMlpH + n0] = c[j][2];
-      P[kOffW2 + (m0 + g + 8) * kMlpH + n0 + 1] = c[j][3];
-    }
-  }
-  // dW1 = dZ1^T X: warp w owns out-tile w/2 and in-tile w%2 (inputs 0..4 kept)
-  {
-    const int m0 = (w >> 1) * 16, n0 = (w & 1) * 8;
-    float c[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int ks = 0; ks < kRows / 16; ++ks) {
-      unsigned a[4];
-      frag_a_T(S.D1T, m0, ks * 16, a);
-      const __nv_bfloat16* b = S.XT + (n0 + g) * kTP + ks * 16 + 2 * t;
-      mma_bf16(c, a, ld_pair(b), ld_pair(b + 8));
-    }
-    const int i0 = n0 + 2 * t;
-    if (i0 < kMlpIn) {
-      P[kOffW1 + (m0 + g) * kMlpIn + i0] = c[0];
-      P[kOffW1 + (m0 + g + 8) * kMlpIn + i0] = c[2];
-    }
-    if (i0 + 1 < kMlpIn) {
-      P[kOffW1 + (m0 + g) * kMlpIn + i0 + 1] = c[1];
-      P[kOffW1 + (m0 + g + 8) * kMlpIn + i0 + 1] = c[3];
-    }
-  }
-  // dW3 = dY^T H2: warp w owns in-tile w (outputs 0..2 kept)
-  {
-    const int n0 = w * 8;
-    float c[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int ks = 0; ks < kRows / 16; ++ks) {
-      unsigned a[4];
-      frag_a_T(S.DYT, 0, ks * 16, a);
-      const __nv_bfloat16* b = S.H2T + (n0 + g) * kTP + ks * 16 + 2 * t;
-      mma_bf16(c, a, ld_pair(b), ld_pair(b + 8));
-    }
-    if (g < kMlpOut) {
-      P[kOffW3 + g * kMlpH + n0 + 2 * t] = c[0];
-      P[kOffW3 + g * kMlpH + n0 + 2 * t + 1] = c[1];
-    }
-  }
-  // biases (fixed order over warps) and the loss
-  for (int i = threadIdx.x; i < kMlpH; i += kThreads) {
-    float s1 = 0.f, s2 = 0.f;
-    for (int ww = 0; ww < 8; ++ww) { s1 += S.db1[ww][i]; s2 += S.db2[ww][i]; }
-    P[kOffB1 + i] = s1;
-    P[kOffB2 + i] = s2;
-  }
-  if (threadIdx.x < kMlpOut) {
-    float s = 0.f;
-    for (int ww = 0; ww < 8; ++ww) s += S.db3[ww][threadIdx.x];
-    P[kOffB3 + threadIdx.x] = s;
-  }
-  if (threadIdx.x == 0) {
-    float s = 0.f;
-    for (int ww = 0; ww < 8; ++ww) s += S.loss[ww];
-    loss_part[blockIdx.x] = s;
   }
 }
 
@@ -470,7 +245,6 @@ __global__ void k_mlp_features(const float* rec, long long n, float dt, const Ml
 
 }  // namespace
 
-size_t mlp_train_smem() { return sizeof(TrainSmem); }
 
 }  // namespace aton
 
@@ -490,6 +264,7 @@ struct aton_mlp {
   double* d_loss = nullptr;
   double* d_acc = nullptr;
   float* d_mm = nullptr;
+  unsigned int* d_err = nullptr;   // tensor-core pipeline waits that gave up (must stay 0)
   int cap_blocks = 0;
   long long step = 0;
   cudaStream_t stream = nullptr;
@@ -536,12 +311,14 @@ int aton_mlp_create(aton_mlp_handle* out, unsigned long long seed) {
       cudaMalloc(&h->norm, sizeof(MlpNorm)) != cudaSuccess ||
       cudaMalloc(&h->d_loss, sizeof(double)) != cudaSuccess ||
       cudaMalloc(&h->d_acc, sizeof(double) * 16 * 148) != cudaSuccess ||
-      cudaMalloc(&h->d_mm, sizeof(float) * 2 * kMlpIn) != cudaSuccess)
+      cudaMalloc(&h->d_mm, sizeof(float) * 2 * kMlpIn) != cudaSuccess ||
+      cudaMalloc(&h->d_err, sizeof(unsigned int)) != cudaSuccess)
     return bail(mfail(ATON_ERR_NOMEM, "cudaMalloc"));
-  if (cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)sizeof(TrainSmem)) != cudaSuccess)
+  if (cudaFuncSetAttribute(k_mlp_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)mlp_train_tc_smem()) != cudaSuccess)
     return bail(mfail(ATON_ERR_CUDA, "train kernel attribute"));
   cudaStream_t s = h->stream;
+  cudaMemsetAsync(h->d_err, 0, sizeof(unsigned int), s);
   cudaMemsetAsync(h->m, 0, sizeof(float) * kMlpParams, s);
   cudaMemsetAsync(h->v, 0, sizeof(float) * kMlpParams, s);
   cudaMemsetAsync(h->img, 0, sizeof(MlpImage), s);   // padding stays zero
@@ -561,7 +338,7 @@ void aton_mlp_destroy(aton_mlp_handle h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   cudaFree(h->theta); cudaFree(h->m); cudaFree(h->v); cudaFree(h->img); cudaFree(h->norm);
   cudaFree(h->partial); cudaFree(h->loss_part); cudaFree(h->d_loss); cudaFree(h->d_acc);
-  cudaFree(h->d_mm);
+  cudaFree(h->d_mm); cudaFree(h->d_err);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -634,14 +411,22 @@ int aton_mlp_forward(aton_mlp_handle h, const float* X, int64_t n, float* Y) {
   return ATON_OK;
 }
 
+// the training kernel's error word (a tensor-core pipeline wait that gave up); call after a sync
+static int check_err(aton_mlp* h) {
+  unsigned int e = 0;
+  MCU(cudaMemcpy(&e, h->d_err, sizeof(e), cudaMemcpyDeviceToHost));
+  if (e) return mfail(ATON_ERR_CUDA, "training kernel: a tensor-core wait gave up");
+  return ATON_OK;
+}
+
 static int train_common(aton_mlp* h, const float* X, const float* T, int n, int adam, float lr,
                         float* grad, double* loss) {
   if (!X || !T || n < 1) return mfail(ATON_ERR_BADARG, "bad argument");
   const int nblk = (n + kRows - 1) / kRows;
   if (int rc = ensure_blocks(h, nblk)) return rc;
   const float inv = 1.f / (float)((double)n * kMlpOut);
-  k_mlp_train<<<nblk, kThreads, sizeof(TrainSmem), h->stream>>>(h->img, X, T, n, inv, h->partial,
-                                                               h->loss_part);
+  k_mlp_train_tc<<<nblk, 128, mlp_train_tc_smem(), h->stream>>>(h->img, X, T, n, inv, h->partial,
+                                                               h->loss_part, h->d_err);
   MCU(cudaGetLastError());
   float bc1 = 1.f, bc2 = 1.f;
   if (adam) {
@@ -657,6 +442,7 @@ static int train_common(aton_mlp* h, const float* X, const float* T, int n, int 
   if (loss) {
     MCU(cudaMemcpyAsync(loss, h->d_loss, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     MCU(cudaStreamSynchronize(h->stream));
+    return check_err(h);
   }
   return ATON_OK;
 }
@@ -679,7 +465,7 @@ int aton_mlp_train_step(aton_mlp_handle h, const float* X, const float* T, int n
 int aton_mlp_synchronize(aton_mlp_handle h) {
   if (!h) return mfail(ATON_ERR_BADARG, "NULL handle");
   MCU(cudaStreamSynchronize(h->stream));
-  return ATON_OK;
+  return check_err(h);
 }
 
 }  // extern "C"

@@ -1,6 +1,8 @@
-// aton_mlp.cuh -- the chemistry-surrogate MLP (5 -> 64 -> 64 -> 3, SiLU) on BF16 tensor cores
-// with FP32 accumulation (mma.sync m16n8k16), shared by the training kernels and the
-// surrogate chemistry kernel.
+// aton_mlp.cuh -- the chemistry-surrogate MLP (5 -> 64 -> 64 -> 3, SiLU): its parameter layout
+// and BF16 weight image, and the inference of a few scattered cells on BF16 tensor cores with
+// FP32 accumulation (warp-level mma.sync m16n8k16: the surrogate kernels run the network for
+// 32 listed cells at a time, far below a 128-row tcgen05 tile; training, on full 128-row tiles,
+// uses tcgen05 in aton_mlp_tc.cu).
 //
 // One warp carries 16 rows through a layer as m16n8k16 products: the accumulator fragments of
 // one layer (16 x 8 tiles, FP32) become, after the activation and a BF16 conversion, the A

@@ -1,0 +1,374 @@
+// aton_mlp_tc.cu -- training step of the chemistry-surrogate MLP (5 -> 64 -> 64 -> 3, SiLU) on the
+// 5th-generation tensor cores (tcgen05): forward and backward of 128 rows per CTA with BF16
+// operands in shared memory and FP32 accumulators in tensor memory (TMEM).
+//
+// One CTA of 128 threads takes 128 rows; thread t owns row t, which is TMEM lane t in every
+// accumulator (M = 128, one row per lane). Thread 0 issues the products (tcgen05.mma,
+// kind::f16, BF16 x BF16 -> FP32) and commits each group to an mbarrier; the threads read the
+// accumulators back with tcgen05.ld, apply the bias and the activation in registers and write
+// the next operands to shared memory. Every operand is stored in the canonical K-major layout
+// without swizzle: 8-row groups of 16-byte rows ("core matrices" of 8 x 8 BF16), the core
+// matrices of a group adjacent along K (128 bytes apart), the groups K * 16 bytes apart.
+//
+//   forward   Z1 = X W1^T (K 16), H1 = silu(Z1 + b1); Z2 = H1 W2^T (K 64), H2 = silu(Z2 + b2);
+//             Y = H2 W3^T + b3 (N padded to 16)
+//   backward  dY = 2 (Y - T) / (rows x 3); dZ2 = (dY W3) * silu'(Z2 + b2) (K 16);
+//             dZ1 = (dZ2 W2) * silu'(Z1 + b1) (K 64)
+//   weights   [dZ2^T; dZ1^T] [H1^T; X^T]^T (M 128, N 80, K = the 128 rows): dW2 in the upper left
+//             block, dW1 in the lower right; [H2^T; dZ2^T] dY (M 128, N 16): dW3^T in the upper
+//             half. (Stacking keeps every product at M = 128; the unused blocks are discarded.)
+//
+// Biases and the loss are summed over the rows in a fixed order. Each CTA writes one FP32
+// partial gradient (the layout of the parameter vector) and its loss; k_mlp_adam sums them.
+// Every mbarrier wait is bounded (2 s): a wait that gives up sets *err, the CTA issues no further
+// products and frees its tensor memory at the end.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "aton_internal.h"
+#include "aton_mlp.cuh"
+
+namespace aton {
+
+namespace {
+
+constexpr int kTcRows = 128;          // rows per CTA = threads = TMEM lanes
+constexpr unsigned kTmemCols = 256;   // columns allocated (power of two >= 32)
+constexpr unsigned kWaitPolls = 1u << 24;
+
+// shared-memory operands (byte offsets; every block 1024-aligned)
+constexpr uint32_t kSmX = 0;                          // X     128 x 16
+constexpr uint32_t kSmW1 = kSmX + 128 * 16 * 2;      // W1     64 x 16
+constexpr uint32_t kSmW2 = kSmW1 + 64 * 16 * 2;      // W2     64 x 64
+constexpr uint32_t kSmW3 = kSmW2 + 64 * 64 * 2;      // W3     16 x 64 (outputs 3..15 zero)
+constexpr uint32_t kSmW2T = kSmW3 + 16 * 64 * 2;     // W2^T   64 x 64
+constexpr uint32_t kSmW3T = kSmW2T + 64 * 64 * 2;    // W3^T   64 x 16
+constexpr uint32_t kSmH1 = kSmW3T + 64 * 16 * 2;     // H1    128 x 64
+constexpr uint32_t kSmH2 = kSmH1 + 128 * 64 * 2;     // H2    128 x 64
+constexpr uint32_t kSmDY = kSmH2 + 128 * 64 * 2;     // dY    128 x 16
+constexpr uint32_t kSmDZ2 = kSmDY + 128 * 16 * 2;    // dZ2   128 x 64
+constexpr uint32_t kSmTA = kSmDZ2 + 128 * 64 * 2;    // [H2^T; dZ2^T; dZ1^T] 192 x 128
+constexpr uint32_t kSmTB = kSmTA + 192 * 128 * 2;    // [H1^T; X^T]           80 x 128
+constexpr uint32_t kSmTC = kSmTB + 80 * 128 * 2;     // dY^T                  16 x 128
+constexpr uint32_t kSmBias = kSmTC + 16 * 128 * 2;   // b1[64], b2[64], b3[16] (FP32)
+constexpr uint32_t kSmRed = kSmBias + 144 * 4;       // per-warp dy sums [4][16], loss [4]
+constexpr uint32_t kSmBar = kSmRed + (4 * 16 + 4) * 4 + 8;   // mbarrier (8-aligned)
+constexpr uint32_t kSmTmem = kSmBar + 8;             // TMEM base written by tcgen05.alloc
+constexpr uint32_t kTcSmem = kSmTmem + 8 + 1024;      // (+ alignment slack of the base)
+// the bias-gradient scratch [128 rows][64] FP32 reuses H1 and H2 (free after layer 3)
+static_assert(kSmH2 == kSmH1 + 128 * 64 * 2, "H1, H2 adjacent");
+static_assert(kSmBar % 8 == 0, "mbarrier alignment");
+
+// byte offset of element (r, k) in a K-major operand with K columns (canonical, no swizzle)
+__device__ __forceinline__ uint32_t kmaj(int r, int k, int K) {
+  return (uint32_t)((r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+// shared-memory matrix descriptor: start address, leading (K) byte offset 128, stride (M/N)
+// byte offset K * 16, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, int K) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) |
+         ((uint64_t)(((unsigned)K * 16u >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// D[tmem] (+)= A B^T for one K = 16 slice
+__device__ __forceinline__ void mma16(uint32_t d, uint64_t a, uint64_t b, uint32_t id, bool acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(id), "r"((uint32_t)acc)
+      : "memory");
+}
+
+// D = A B^T over K (a multiple of 16): a, b are the operands' shared addresses, both K-major
+__device__ __forceinline__ void gemm(uint32_t d, uint32_t a, uint32_t b, int K, uint32_t id) {
+  for (int ks = 0; ks < K / 16; ++ks)
+    mma16(d, sdesc(a + ks * 256u, K), sdesc(b + ks * 256u, K), id, ks > 0);
+}
+
+__device__ __forceinline__ void commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   bar)
+               : "memory");
+}
+
+// bounded wait for the given phase parity of the mbarrier: gives up after kWaitPolls polls or
+// 2 s (each poll may suspend the thread for up to 2 us until the phase completes)
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
+  unsigned long long t0 = 0;
+  for (unsigned i = 0; i < kWaitPolls; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity), "r"(2000u)
+        : "memory");
+    if (done) return true;
+    unsigned long long now;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+    if (i == 0) t0 = now;
+    else if (now - t0 > 2000000000ull) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void put_bf16(unsigned char* sm, uint32_t off, float v) {
+  *reinterpret_cast<__nv_bfloat16*>(sm + off) = __float2bfloat16(v);
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kTcRows, 1)
+    k_mlp_train_tc(const MlpImage* __restrict__ img, const float* __restrict__ X,
+                   const float* __restrict__ T, int n, float inv_count, float* partial,
+                   float* loss_part, unsigned int* err) {
+  extern __shared__ __align__(1024) unsigned char tc_raw[];
+  unsigned char* sm = tc_raw + ((1024u - (su32(tc_raw) & 1023u)) & 1023u);
+  const uint32_t sb = su32(sm);
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const int row = blockIdx.x * kTcRows + t;
+  const bool valid = row < n;
+  float* bias = reinterpret_cast<float*>(sm + kSmBias);
+  float* red = reinterpret_cast<float*>(sm + kSmRed);
+  const uint32_t bar = sb + kSmBar;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kSmTmem);
+
+  // operands that do not depend on the rows: the weights in K-major layout, zero padding
+  for (int i = t; i < 64 * 16; i += kTcRows) {   // W1 (64 x 16), W3^T (64 x 16)
+    const int o = i >> 4, k = i & 15;
+    *reinterpret_cast<__nv_bfloat16*>(sm + kSmW1 + kmaj(o, k, 16)) = img->W1[o * kP1 + k];
+    *reinterpret_cast<__nv_bfloat16*>(sm + kSmW3T + kmaj(o, k, 16)) = img->W3T[o * kP3T + k];
+  }
+  for (int i = t; i < 64 * 64; i += kTcRows) {   // W2, W2^T (64 x 64)
+    const int o = i >> 6, k = i & 63;
+    *reinterpret_cast<__nv_bfloat16*>(sm + kSmW2 + kmaj(o, k, 64)) = img->W2[o * kP2 + k];
+    *reinterpret_cast<__nv_bfloat16*>(sm + kSmW2T + kmaj(o, k, 64)) = img->W2T[o * kP2 + k];
+  }
+  for (int i = t; i < 16 * 64; i += kTcRows) {   // W3 (16 x 64; the image holds 8 rows)
+    const int o = i >> 6, k = i & 63;
+    const __nv_bfloat16 v = o < 8 ? img->W3[o * kP2 + k] : __float2bfloat16(0.f);
+    *reinterpret_cast<__nv_bfloat16*>(sm + kSmW3 + kmaj(o, k, 64)) = v;
+  }
+  for (int i = t; i < 144; i += kTcRows)
+    bias[i] = i < 64 ? img->b1[i] : (i < 128 ? img->b2[i - 64] : img->b3[i - 128]);
+  // this row's input: X (16 columns, 5 used) and its transposed copy (rows 64..79 of TB)
+  float x[kMlpIn];
+#pragma unroll
+  for (int k = 0; k < kMlpIn; ++k) x[k] = valid ? X[(size_t)row * kMlpIn + k] : 0.f;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const float v = k < kMlpIn ? x[k] : 0.f;
+    put_bf16(sm, kSmX + kmaj(t, k, 16), v);
+    put_bf16(sm, kSmTB + kmaj(64 + k, t, 128), v);
+  }
+  float tg[kMlpOut];
+#pragma unroll
+  for (int k = 0; k < kMlpOut; ++k) tg[k] = valid ? T[(size_t)row * kMlpOut + k] : 0.f;
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (w == 0) {   // TMEM: 256 columns x 128 lanes of FP32
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     sb + kSmTmem),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tm = *tmem_slot;
+  const uint32_t lane_base = tm + ((uint32_t)(32 * w) << 16);   // this warp's TMEM lanes
+  // TMEM columns: Z1 [0, 64), Z2 then dH1 [64, 128), Y [128, 144), dH2 [144, 208);
+  // afterwards the weight products: D' [0, 80), D'' [128, 144)
+  const uint32_t cZ1 = 0, cZ2 = 64, cY = 128, cH2 = 144;
+  bool ok = true;
+  uint32_t phase = 0;
+  // issue (thread 0) a group of products and wait for it (every thread)
+  auto run = [&](auto issue) {
+    if (t == 0) {
+      fence_after();
+      if (ok) issue();
+      commit(bar);
+    }
+    if (!bar_wait(bar, phase & 1)) ok = false;
+    ++phase;
+    fence_after();
+  };
+  // operands written by the threads -> visible to the tensor cores; TMEM reads done
+  auto handoff = [&]() {
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+  };
+
+  // ---- layer 1: Z1 = X W1^T
+  run([&] { gemm(tm + cZ1, sb + kSmX, sb + kSmW1, 16, idesc(128, 64)); });
+  float z[16];
+  for (int c = 0; c < 64; c += 16) {
+    tld16(lane_base + cZ1 + c, z);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const float h = silu(z[j] + bias[c + j]);
+      put_bf16(sm, kSmH1 + kmaj(t, c + j, 64), h);
+      put_bf16(sm, kSmTB + kmaj(c + j, t, 128), h);   // H1^T (rows 0..63 of TB)
+    }
+  }
+  handoff();
+  // ---- layer 2: Z2 = H1 W2^T
+  run([&] { gemm(tm + cZ2, sb + kSmH1, sb + kSmW2, 64, idesc(128, 64)); });
+  for (int c = 0; c < 64; c += 16) {
+    tld16(lane_base + cZ2 + c, z);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const float h = silu(z[j] + bias[64 + c + j]);
+      put_bf16(sm, kSmH2 + kmaj(t, c + j, 64), h);
+      put_bf16(sm, kSmTA + kmaj(c + j, t, 128), h);   // H2^T (rows 0..63 of TA)
+    }
+  }
+  handoff();
+  // ---- layer 3: Y = H2 W3^T + b3; dY = 2 (Y - T) / (rows x 3); the loss
+  run([&] { gemm(tm + cY, sb + kSmH2, sb + kSmW3, 64, idesc(128, 16)); });
+  float dy[kMlpOut], sq = 0.f;
+  tld16(lane_base + cY, z);
+#pragma unroll
+  for (int k = 0; k < kMlpOut; ++k) {
+    const float d = valid ? z[k] + bias[128 + k] - tg[k] : 0.f;
+    dy[k] = 2.f * d * inv_count;
+    sq += d * d;
+  }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const float v = k < kMlpOut ? dy[k] : 0.f;
+    put_bf16(sm, kSmDY + kmaj(t, k, 16), v);
+    put_bf16(sm, kSmTC + kmaj(k, t, 128), v);        // dY^T
+  }
+  // per-warp sums of dy (db3) and of the squared error, in lane order
+#pragma unroll
+  for (int k = 0; k < kMlpOut; ++k) {
+    float s = dy[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) red[w * 16 + k] = s;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if (lane == 0) red[64 + w] = sq;
+  handoff();
+  // ---- dH2 = dY W3 (B = W3^T, K = 16 outputs)
+  run([&] { gemm(tm + cH2, sb + kSmDY, sb + kSmW3T, 16, idesc(128, 64)); });
+  // dZ2 = dH2 * silu'(Z2 + b2); the row's dz2 also to the bias scratch (skewed columns)
+  float* scr = reinterpret_cast<float*>(sm + kSmH1);   // [128][64] FP32 over H1, H2
+  for (int c = 0; c < 64; c += 16) {
+    float g[16];
+    tld16(lane_base + cZ2 + c, z);
+    tld16(lane_base + cH2 + c, g);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const float d = g[j] * dsilu(z[j] + bias[64 + c + j]);
+      put_bf16(sm, kSmDZ2 + kmaj(t, c + j, 64), d);
+      put_bf16(sm, kSmTA + kmaj(64 + c + j, t, 128), d);   // dZ2^T (rows 64..127 of TA)
+      scr[t * 64 + ((c + j + t) & 63)] = d;
+    }
+  }
+  handoff();
+  // db2: column sums over the rows in row order
+  float db2 = 0.f;
+  if (t < 64)
+    for (int r = 0; r < kTcRows; ++r) db2 += scr[r * 64 + ((t + r) & 63)];
+  __syncthreads();   // (the scratch is rewritten below)
+  // ---- dH1 = dZ2 W2 (B = W2^T, K = 64) into the columns of Z2
+  run([&] { gemm(tm + cZ2, sb + kSmDZ2, sb + kSmW2T, 64, idesc(128, 64)); });
+  for (int c = 0; c < 64; c += 16) {
+    float g[16];
+    tld16(lane_base + cZ1 + c, z);
+    tld16(lane_base + cZ2 + c, g);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const float d = g[j] * dsilu(z[j] + bias[c + j]);
+      put_bf16(sm, kSmTA + kmaj(128 + c + j, t, 128), d);   // dZ1^T (rows 128..191 of TA)
+      scr[t * 64 + ((c + j + t) & 63)] = d;
+    }
+  }
+  handoff();
+  float db1 = 0.f;
+  if (t < 64)
+    for (int r = 0; r < kTcRows; ++r) db1 += scr[r * 64 + ((t + r) & 63)];
+  // ---- weight gradients: [dZ2^T; dZ1^T] [H1^T; X^T]^T and [H2^T; dZ2^T] [dY^T]^T over the rows
+  run([&] {
+    gemm(tm + 0, sb + kSmTA + 64 * 128 * 2, sb + kSmTB, 128, idesc(128, 80));
+    gemm(tm + cY, sb + kSmTA, sb + kSmTC, 128, idesc(128, 16));
+  });
+  float* P = partial + (size_t)blockIdx.x * kMlpParams;
+  for (int c = 0; c < 80; c += 16) {
+    tld16(lane_base + c, z);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int col = c + j;
+      if (t < 64 && col < 64) P[kOffW2 + t * kMlpH + col] = ok ? z[j] : 0.f;   // dW2[t][col]
+      if (t >= 64 && col >= 64 && col - 64 < kMlpIn)                        // dW1[t-64][i]
+        P[kOffW1 + (t - 64) * kMlpIn + (col - 64)] = ok ? z[j] : 0.f;
+    }
+  }
+  tld16(lane_base + cY, z);
+  if (t < 64)
+#pragma unroll
+    for (int k = 0; k < kMlpOut; ++k) P[kOffW3 + k * kMlpH + t] = ok ? z[k] : 0.f;   // dW3[k][t]
+  if (t < 64) {
+    P[kOffB1 + t] = db1;
+    P[kOffB2 + t] = db2;
+  }
+  if (t < kMlpOut) P[kOffB3 + t] = red[t] + red[16 + t] + red[32 + t] + red[48 + t];
+  if (t == 0) loss_part[blockIdx.x] = red[64] + red[65] + red[66] + red[67];
+  if (!ok && t == 0) atomicAdd(err, 1u);
+  fence_before();
+  __syncthreads();
+  if (w == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+size_t mlp_train_tc_smem() { return kTcSmem; }
+
+}  // namespace aton
