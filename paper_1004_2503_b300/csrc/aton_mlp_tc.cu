@@ -6,20 +6,25 @@
 // accumulator (M = 128, one row per lane). Thread 0 issues the products (tcgen05.mma,
 // kind::f16, BF16 x BF16 -> FP32) and commits each group to an mbarrier; the threads read the
 // accumulators back with tcgen05.ld, apply the bias and the activation in registers and write
-// the next operands to shared memory. Every operand is stored in the canonical K-major layout
-// without swizzle: 8-row groups of 16-byte rows ("core matrices" of 8 x 8 BF16), the core
-// matrices of a group adjacent along K (128 bytes apart), the groups K * 16 bytes apart.
+// the next operands to shared memory, a row's 8 consecutive features as one 16-byte store.
+// Every activation buffer holds [row][feature] in the canonical layout without swizzle: 8 x 8
+// BF16 "core matrices" of 128 bytes (8 rows of 16 bytes, one row's 8 consecutive features),
+// the core matrices of an 8-row group 128 bytes apart along the features, the 8-row groups
+// (pitch x 16) bytes apart. A product reads such a buffer either K-major (its rows are the
+// product's M or N rows, its features the contraction) or, for the weight gradients, MN-major
+// (its features are the product's rows and the contraction runs over the 128 rows): the same
+// bytes, the transposed copy never written.
 //
 //   forward   Z1 = X W1^T (K 16), H1 = silu(Z1 + b1); Z2 = H1 W2^T (K 64), H2 = silu(Z2 + b2);
 //             Y = H2 W3^T + b3 (N padded to 16)
 //   backward  dY = 2 (Y - T) / (rows x 3); dZ2 = (dY W3) * silu'(Z2 + b2) (K 16);
 //             dZ1 = (dZ2 W2) * silu'(Z1 + b1) (K 64)
-//   weights   [dZ2^T; dZ1^T] [H1^T; X^T]^T (M 128, N 80, K = the 128 rows): dW2 in the upper left
-//             block, dW1 in the lower right; [H2^T; dZ2^T] dY (M 128, N 16): dW3^T in the upper
-//             half. (Stacking keeps every product at M = 128; the unused blocks are discarded.)
+//   weights   [dZ2 | dZ1]^T [H1 | X | 1]  (M 128, N 96, K = the 128 rows): dW2 in the upper left
+//             block, dW1 in the lower middle, the bias gradients db2, db1 in the column of ones;
+//             H2^T dY (M 128, N 16; rows 64..127 unused): dW3^T. (Both keep M = 128.)
 //
-// Biases and the loss are summed over the rows in a fixed order. Each CTA writes one FP32
-// partial gradient (the layout of the parameter vector) and its loss; k_mlp_adam sums them.
+// db3 and the loss are summed over the rows in a fixed order. Each CTA writes one FP32 partial
+// gradient (the layout of the parameter vector) and its loss; k_mlp_adam sums them.
 // Every mbarrier wait is bounded (2 s): a wait that gives up sets *err, the CTA issues no further
 // products and frees its tensor memory at the end.
 #include <cuda_bf16.h>
@@ -37,45 +42,53 @@ constexpr int kTcRows = 128;          // rows per CTA = threads = TMEM lanes
 constexpr unsigned kTmemCols = 256;   // columns allocated (power of two >= 32)
 constexpr unsigned kWaitPolls = 1u << 24;
 
-// shared-memory operands (byte offsets; every block 1024-aligned)
-constexpr uint32_t kSmX = 0;                          // X     128 x 16
-constexpr uint32_t kSmW1 = kSmX + 128 * 16 * 2;      // W1     64 x 16
-constexpr uint32_t kSmW2 = kSmW1 + 64 * 16 * 2;      // W2     64 x 64
-constexpr uint32_t kSmW3 = kSmW2 + 64 * 64 * 2;      // W3     16 x 64 (outputs 3..15 zero)
-constexpr uint32_t kSmW2T = kSmW3 + 16 * 64 * 2;     // W2^T   64 x 64
-constexpr uint32_t kSmW3T = kSmW2T + 64 * 64 * 2;    // W3^T   64 x 16
-constexpr uint32_t kSmH1 = kSmW3T + 64 * 16 * 2;     // H1    128 x 64
-constexpr uint32_t kSmH2 = kSmH1 + 128 * 64 * 2;     // H2    128 x 64
-constexpr uint32_t kSmDY = kSmH2 + 128 * 64 * 2;     // dY    128 x 16
-constexpr uint32_t kSmDZ2 = kSmDY + 128 * 16 * 2;    // dZ2   128 x 64
-constexpr uint32_t kSmTA = kSmDZ2 + 128 * 64 * 2;    // [H2^T; dZ2^T; dZ1^T] 192 x 128
-constexpr uint32_t kSmTB = kSmTA + 192 * 128 * 2;    // [H1^T; X^T]           80 x 128
-constexpr uint32_t kSmTC = kSmTB + 80 * 128 * 2;     // dY^T                  16 x 128
-constexpr uint32_t kSmBias = kSmTC + 16 * 128 * 2;   // b1[64], b2[64], b3[16] (FP32)
-constexpr uint32_t kSmRed = kSmBias + 144 * 4;       // per-warp dy sums [4][16], loss [4]
+// shared-memory buffers (byte offsets; every block 1024-aligned), [row][feature] canonical
+constexpr int kPHX = 96;                             // HX: H1 0..63, X 64..79, 1 at 80, 0 81..95
+constexpr int kPH2 = 64, kPDZ = 128, kPDY = 16;      // H2; dZ2 0..63 and dZ1 64..127; dY (3 used)
+constexpr uint32_t kSmHX = 0;
+constexpr uint32_t kSmH2 = kSmHX + 128 * kPHX * 2;
+constexpr uint32_t kSmDZ = kSmH2 + 128 * kPH2 * 2;
+constexpr uint32_t kSmDY = kSmDZ + 128 * kPDZ * 2;
+constexpr uint32_t kSmW1 = kSmDY + 128 * kPDY * 2;    // W1     64 x 16 (inputs 5..15 zero)
+constexpr uint32_t kSmW2 = kSmW1 + 64 * 16 * 2;       // W2     64 x 64
+constexpr uint32_t kSmW3 = kSmW2 + 64 * 64 * 2;       // W3     16 x 64 (outputs 3..15 zero)
+constexpr uint32_t kSmW2T = kSmW3 + 16 * 64 * 2;      // W2^T   64 x 64
+constexpr uint32_t kSmW3T = kSmW2T + 64 * 64 * 2;     // W3^T   64 x 16
+constexpr uint32_t kSmBias = kSmW3T + 64 * 16 * 2;    // b1[64], b2[64], b3[16] (FP32)
+constexpr uint32_t kSmRed = kSmBias + 144 * 4;        // per-warp dy sums [4][16], loss [4]
 constexpr uint32_t kSmBar = kSmRed + (4 * 16 + 4) * 4 + 8;   // mbarrier (8-aligned)
-constexpr uint32_t kSmTmem = kSmBar + 8;             // TMEM base written by tcgen05.alloc
+constexpr uint32_t kSmTmem = kSmBar + 8;              // TMEM base written by tcgen05.alloc
 constexpr uint32_t kTcSmem = kSmTmem + 8 + 1024;      // (+ alignment slack of the base)
-// the bias-gradient scratch [128 rows][64] FP32 reuses H1 and H2 (free after layer 3)
-static_assert(kSmH2 == kSmH1 + 128 * 64 * 2, "H1, H2 adjacent");
 static_assert(kSmBar % 8 == 0, "mbarrier alignment");
+static_assert(kSmDZ - kSmH2 + 128 * kPDZ * 2 >= 17280, "the M = 128 view of H2 stays in bounds");
 
-// byte offset of element (r, k) in a K-major operand with K columns (canonical, no swizzle)
-__device__ __forceinline__ uint32_t kmaj(int r, int k, int K) {
-  return (uint32_t)((r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+// byte offset of element (r, c) in a [row][feature] buffer of pitch P features (canonical)
+__device__ __forceinline__ uint32_t cano(int r, int c, int P) {
+  return (uint32_t)((r >> 3) * (P * 16) + (c >> 3) * 128 + (r & 7) * 16 + (c & 7) * 2);
 }
 
-// shared-memory matrix descriptor: start address, leading (K) byte offset 128, stride (M/N)
-// byte offset K * 16, descriptor version 1, no swizzle
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, int K) {
-  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) |
-         ((uint64_t)(((unsigned)K * 16u >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+// shared-memory matrix descriptor, no swizzle, descriptor version 1: start address, leading
+// byte offset (between core matrices adjacent along the contraction) and stride byte offset
+// (between core matrices adjacent along the product's rows)
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// a [row][feature] buffer of pitch P read K-major (the features are the contraction: 128 bytes
+// between feature groups, P x 16 between 8-row groups) or MN-major (the rows are the
+// contraction: the same two offsets in the other roles)
+__device__ __forceinline__ uint64_t sdesc_k(uint32_t saddr, int P) {
+  return sdesc(saddr, 128u, (uint32_t)P * 16u);
+}
+__device__ __forceinline__ uint64_t sdesc_mn(uint32_t saddr, int P) {
+  return sdesc(saddr, (uint32_t)P * 16u, 128u);
 }
 
-// instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, both K-major, M x N
-__host__ __device__ constexpr uint32_t idesc(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
+// instruction descriptor, kind::f16: FP32 accumulator, BF16 A and B, M x N; tA / tB set: the
+// operand is MN-major
+__host__ __device__ constexpr uint32_t idesc(int M, int N, bool tA = false, bool tB = false) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)tA << 15) | ((uint32_t)tB << 16) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -91,10 +104,19 @@ __device__ __forceinline__ void mma16(uint32_t d, uint64_t a, uint64_t b, uint32
       : "memory");
 }
 
-// D = A B^T over K (a multiple of 16): a, b are the operands' shared addresses, both K-major
-__device__ __forceinline__ void gemm(uint32_t d, uint32_t a, uint32_t b, int K, uint32_t id) {
+// D = A B^T over K (a multiple of 16), both operands K-major: a, b are their first elements,
+// pa, pb their buffers' pitches (a K = 16 slice is two core matrices along the features)
+__device__ __forceinline__ void gemm_k(uint32_t d, uint32_t a, int pa, uint32_t b, int pb, int K,
+                                       uint32_t id) {
   for (int ks = 0; ks < K / 16; ++ks)
-    mma16(d, sdesc(a + ks * 256u, K), sdesc(b + ks * 256u, K), id, ks > 0);
+    mma16(d, sdesc_k(a + ks * 256u, pa), sdesc_k(b + ks * 256u, pb), id, ks > 0);
+}
+// D = A B^T over the 128 rows of both buffers, both MN-major (their features are the product's
+// rows): a K = 16 slice is two 8-row groups
+__device__ __forceinline__ void gemm_mn(uint32_t d, uint32_t a, int pa, uint32_t b, int pb,
+                                        uint32_t id) {
+  for (int ks = 0; ks < 128 / 16; ++ks)
+    mma16(d, sdesc_mn(a + ks * 32u * pa, pa), sdesc_mn(b + ks * 32u * pb, pb), id, ks > 0);
 }
 
 __device__ __forceinline__ void commit(uint32_t bar) {
@@ -149,13 +171,19 @@ __device__ __forceinline__ void tld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void put_bf16(unsigned char* sm, uint32_t off, float v) {
-  *reinterpret_cast<__nv_bfloat16*>(sm + off) = __float2bfloat16(v);
+// 8 consecutive features of a row (one 16-byte store)
+__device__ __forceinline__ void put8(unsigned char* sm, uint32_t off, const float* v) {
+  uint4 q;
+  q.x = pack_bf16(v[0], v[1]);
+  q.y = pack_bf16(v[2], v[3]);
+  q.z = pack_bf16(v[4], v[5]);
+  q.w = pack_bf16(v[6], v[7]);
+  *reinterpret_cast<uint4*>(sm + off) = q;
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(kTcRows, 1)
+__global__ void __launch_bounds__(kTcRows, 2)
     k_mlp_train_tc(const MlpImage* __restrict__ img, const float* __restrict__ X,
                    const float* __restrict__ T, int n, float inv_count, float* partial,
                    float* loss_part, unsigned int* err) {
@@ -170,33 +198,35 @@ __global__ void __launch_bounds__(kTcRows, 1)
   const uint32_t bar = sb + kSmBar;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kSmTmem);
 
-  // operands that do not depend on the rows: the weights in K-major layout, zero padding
+  // the weights in K-major layout (their rows the products' N rows), zero padding
   for (int i = t; i < 64 * 16; i += kTcRows) {   // W1 (64 x 16), W3^T (64 x 16)
     const int o = i >> 4, k = i & 15;
-    *reinterpret_cast<__nv_bfloat16*>(sm + kSmW1 + kmaj(o, k, 16)) = img->W1[o * kP1 + k];
-    *reinterpret_cast<__nv_bfloat16*>(sm + kSmW3T + kmaj(o, k, 16)) = img->W3T[o * kP3T + k];
+    *reinterpret_cast<__nv_bfloat16*>(sm + kSmW1 + cano(o, k, 16)) = img->W1[o * kP1 + k];
+    *reinterpret_cast<__nv_bfloat16*>(sm + kSmW3T + cano(o, k, 16)) = img->W3T[o * kP3T + k];
   }
   for (int i = t; i < 64 * 64; i += kTcRows) {   // W2, W2^T (64 x 64)
     const int o = i >> 6, k = i & 63;
-    *reinterpret_cast<__nv_bfloat16*>(sm + kSmW2 + kmaj(o, k, 64)) = img->W2[o * kP2 + k];
-    *reinterpret_cast<__nv_bfloat16*>(sm + kSmW2T + kmaj(o, k, 64)) = img->W2T[o * kP2 + k];
+    *reinterpret_cast<__nv_bfloat16*>(sm + kSmW2 + cano(o, k, 64)) = img->W2[o * kP2 + k];
+    *reinterpret_cast<__nv_bfloat16*>(sm + kSmW2T + cano(o, k, 64)) = img->W2T[o * kP2 + k];
   }
   for (int i = t; i < 16 * 64; i += kTcRows) {   // W3 (16 x 64; the image holds 8 rows)
     const int o = i >> 6, k = i & 63;
     const __nv_bfloat16 v = o < 8 ? img->W3[o * kP2 + k] : __float2bfloat16(0.f);
-    *reinterpret_cast<__nv_bfloat16*>(sm + kSmW3 + kmaj(o, k, 64)) = v;
+    *reinterpret_cast<__nv_bfloat16*>(sm + kSmW3 + cano(o, k, 64)) = v;
   }
   for (int i = t; i < 144; i += kTcRows)
     bias[i] = i < 64 ? img->b1[i] : (i < 128 ? img->b2[i - 64] : img->b3[i - 128]);
-  // this row's input: X (16 columns, 5 used) and its transposed copy (rows 64..79 of TB)
-  float x[kMlpIn];
+  // this row's input into HX features 64..79 (5 used), the column of ones (80) and zeros
+  {
+    float v[16];
 #pragma unroll
-  for (int k = 0; k < kMlpIn; ++k) x[k] = valid ? X[(size_t)row * kMlpIn + k] : 0.f;
+    for (int k = 0; k < 16; ++k) v[k] = valid && k < kMlpIn ? X[(size_t)row * kMlpIn + k] : 0.f;
+    put8(sm, kSmHX + cano(t, 64, kPHX), v);
+    put8(sm, kSmHX + cano(t, 72, kPHX), v + 8);
 #pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    const float v = k < kMlpIn ? x[k] : 0.f;
-    put_bf16(sm, kSmX + kmaj(t, k, 16), v);
-    put_bf16(sm, kSmTB + kmaj(64 + k, t, 128), v);
+    for (int k = 0; k < 16; ++k) v[k] = k == 0 ? 1.f : 0.f;
+    put8(sm, kSmHX + cano(t, 80, kPHX), v);
+    put8(sm, kSmHX + cano(t, 88, kPHX), v + 8);
   }
   float tg[kMlpOut];
 #pragma unroll
@@ -219,7 +249,7 @@ __global__ void __launch_bounds__(kTcRows, 1)
   const uint32_t tm = *tmem_slot;
   const uint32_t lane_base = tm + ((uint32_t)(32 * w) << 16);   // this warp's TMEM lanes
   // TMEM columns: Z1 [0, 64), Z2 then dH1 [64, 128), Y [128, 144), dH2 [144, 208);
-  // afterwards the weight products: D' [0, 80), D'' [128, 144)
+  // afterwards the weight products: D' [0, 96), D'' [128, 144)
   const uint32_t cZ1 = 0, cZ2 = 64, cY = 128, cH2 = 144;
   bool ok = true;
   uint32_t phase = 0;
@@ -240,34 +270,30 @@ __global__ void __launch_bounds__(kTcRows, 1)
     fence_before();
     __syncthreads();
   };
+  float z[16], g[16], v[16];
 
   // ---- layer 1: Z1 = X W1^T
-  run([&] { gemm(tm + cZ1, sb + kSmX, sb + kSmW1, 16, idesc(128, 64)); });
-  float z[16];
+  run([&] { gemm_k(tm + cZ1, sb + kSmHX + 8 * 128, kPHX, sb + kSmW1, 16, 16, idesc(128, 64)); });
   for (int c = 0; c < 64; c += 16) {
     tld16(lane_base + cZ1 + c, z);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const float h = silu(z[j] + bias[c + j]);
-      put_bf16(sm, kSmH1 + kmaj(t, c + j, 64), h);
-      put_bf16(sm, kSmTB + kmaj(c + j, t, 128), h);   // H1^T (rows 0..63 of TB)
-    }
+    for (int j = 0; j < 16; ++j) v[j] = silu(z[j] + bias[c + j]);
+    put8(sm, kSmHX + cano(t, c, kPHX), v);
+    put8(sm, kSmHX + cano(t, c + 8, kPHX), v + 8);
   }
   handoff();
   // ---- layer 2: Z2 = H1 W2^T
-  run([&] { gemm(tm + cZ2, sb + kSmH1, sb + kSmW2, 64, idesc(128, 64)); });
+  run([&] { gemm_k(tm + cZ2, sb + kSmHX, kPHX, sb + kSmW2, 64, 64, idesc(128, 64)); });
   for (int c = 0; c < 64; c += 16) {
     tld16(lane_base + cZ2 + c, z);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const float h = silu(z[j] + bias[64 + c + j]);
-      put_bf16(sm, kSmH2 + kmaj(t, c + j, 64), h);
-      put_bf16(sm, kSmTA + kmaj(c + j, t, 128), h);   // H2^T (rows 0..63 of TA)
-    }
+    for (int j = 0; j < 16; ++j) v[j] = silu(z[j] + bias[64 + c + j]);
+    put8(sm, kSmH2 + cano(t, c, kPH2), v);
+    put8(sm, kSmH2 + cano(t, c + 8, kPH2), v + 8);
   }
   handoff();
   // ---- layer 3: Y = H2 W3^T + b3; dY = 2 (Y - T) / (rows x 3); the loss
-  run([&] { gemm(tm + cY, sb + kSmH2, sb + kSmW3, 64, idesc(128, 16)); });
+  run([&] { gemm_k(tm + cY, sb + kSmH2, kPH2, sb + kSmW3, 64, 64, idesc(128, 16)); });
   float dy[kMlpOut], sq = 0.f;
   tld16(lane_base + cY, z);
 #pragma unroll
@@ -277,11 +303,9 @@ __global__ void __launch_bounds__(kTcRows, 1)
     sq += d * d;
   }
 #pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    const float v = k < kMlpOut ? dy[k] : 0.f;
-    put_bf16(sm, kSmDY + kmaj(t, k, 16), v);
-    put_bf16(sm, kSmTC + kmaj(k, t, 128), v);        // dY^T
-  }
+  for (int k = 0; k < 16; ++k) v[k] = k < kMlpOut ? dy[k] : 0.f;
+  put8(sm, kSmDY + cano(t, 0, kPDY), v);
+  put8(sm, kSmDY + cano(t, 8, kPDY), v + 8);
   // per-warp sums of dy (db3) and of the squared error, in lane order
 #pragma unroll
   for (int k = 0; k < kMlpOut; ++k) {
@@ -295,68 +319,51 @@ __global__ void __launch_bounds__(kTcRows, 1)
   if (lane == 0) red[64 + w] = sq;
   handoff();
   // ---- dH2 = dY W3 (B = W3^T, K = 16 outputs)
-  run([&] { gemm(tm + cH2, sb + kSmDY, sb + kSmW3T, 16, idesc(128, 64)); });
-  // dZ2 = dH2 * silu'(Z2 + b2); the row's dz2 also to the bias scratch (skewed columns)
-  float* scr = reinterpret_cast<float*>(sm + kSmH1);   // [128][64] FP32 over H1, H2
+  run([&] { gemm_k(tm + cH2, sb + kSmDY, kPDY, sb + kSmW3T, 16, 16, idesc(128, 64)); });
+  // dZ2 = dH2 * silu'(Z2 + b2) into DZ features 0..63
   for (int c = 0; c < 64; c += 16) {
-    float g[16];
     tld16(lane_base + cZ2 + c, z);
     tld16(lane_base + cH2 + c, g);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const float d = g[j] * dsilu(z[j] + bias[64 + c + j]);
-      put_bf16(sm, kSmDZ2 + kmaj(t, c + j, 64), d);
-      put_bf16(sm, kSmTA + kmaj(64 + c + j, t, 128), d);   // dZ2^T (rows 64..127 of TA)
-      scr[t * 64 + ((c + j + t) & 63)] = d;
-    }
+    for (int j = 0; j < 16; ++j) v[j] = g[j] * dsilu(z[j] + bias[64 + c + j]);
+    put8(sm, kSmDZ + cano(t, c, kPDZ), v);
+    put8(sm, kSmDZ + cano(t, c + 8, kPDZ), v + 8);
   }
   handoff();
-  // db2: column sums over the rows in row order
-  float db2 = 0.f;
-  if (t < 64)
-    for (int r = 0; r < kTcRows; ++r) db2 += scr[r * 64 + ((t + r) & 63)];
-  __syncthreads();   // (the scratch is rewritten below)
   // ---- dH1 = dZ2 W2 (B = W2^T, K = 64) into the columns of Z2
-  run([&] { gemm(tm + cZ2, sb + kSmDZ2, sb + kSmW2T, 64, idesc(128, 64)); });
+  run([&] { gemm_k(tm + cZ2, sb + kSmDZ, kPDZ, sb + kSmW2T, 64, 64, idesc(128, 64)); });
+  // dZ1 = dH1 * silu'(Z1 + b1) into DZ features 64..127
   for (int c = 0; c < 64; c += 16) {
-    float g[16];
     tld16(lane_base + cZ1 + c, z);
     tld16(lane_base + cZ2 + c, g);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const float d = g[j] * dsilu(z[j] + bias[c + j]);
-      put_bf16(sm, kSmTA + kmaj(128 + c + j, t, 128), d);   // dZ1^T (rows 128..191 of TA)
-      scr[t * 64 + ((c + j + t) & 63)] = d;
-    }
+    for (int j = 0; j < 16; ++j) v[j] = g[j] * dsilu(z[j] + bias[c + j]);
+    put8(sm, kSmDZ + cano(t, 64 + c, kPDZ), v);
+    put8(sm, kSmDZ + cano(t, 64 + c + 8, kPDZ), v + 8);
   }
   handoff();
-  float db1 = 0.f;
-  if (t < 64)
-    for (int r = 0; r < kTcRows; ++r) db1 += scr[r * 64 + ((t + r) & 63)];
-  // ---- weight gradients: [dZ2^T; dZ1^T] [H1^T; X^T]^T and [H2^T; dZ2^T] [dY^T]^T over the rows
+  // ---- weight and bias gradients over the rows: [dZ2 | dZ1]^T [H1 | X | 1], H2^T dY
   run([&] {
-    gemm(tm + 0, sb + kSmTA + 64 * 128 * 2, sb + kSmTB, 128, idesc(128, 80));
-    gemm(tm + cY, sb + kSmTA, sb + kSmTC, 128, idesc(128, 16));
+    gemm_mn(tm + 0, sb + kSmDZ, kPDZ, sb + kSmHX, kPHX, idesc(128, 96, true, true));
+    gemm_mn(tm + cY, sb + kSmH2, kPH2, sb + kSmDY, kPDY, idesc(128, 16, true, true));
   });
   float* P = partial + (size_t)blockIdx.x * kMlpParams;
-  for (int c = 0; c < 80; c += 16) {
+  for (int c = 0; c < 96; c += 16) {
     tld16(lane_base + c, z);
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
       const int col = c + j;
-      if (t < 64 && col < 64) P[kOffW2 + t * kMlpH + col] = ok ? z[j] : 0.f;   // dW2[t][col]
-      if (t >= 64 && col >= 64 && col - 64 < kMlpIn)                        // dW1[t-64][i]
-        P[kOffW1 + (t - 64) * kMlpIn + (col - 64)] = ok ? z[j] : 0.f;
+      const float val = ok ? z[j] : 0.f;
+      if (t < 64 && col < 64) P[kOffW2 + t * kMlpH + col] = val;                  // dW2[t][col]
+      if (t >= 64 && col >= 64 && col - 64 < kMlpIn)
+        P[kOffW1 + (t - 64) * kMlpIn + (col - 64)] = val;                          // dW1
+      if (col == 80) P[t < 64 ? kOffB2 + t : kOffB1 + (t - 64)] = val;            // db2, db1
     }
   }
   tld16(lane_base + cY, z);
   if (t < 64)
 #pragma unroll
     for (int k = 0; k < kMlpOut; ++k) P[kOffW3 + k * kMlpH + t] = ok ? z[k] : 0.f;   // dW3[k][t]
-  if (t < 64) {
-    P[kOffB1 + t] = db1;
-    P[kOffB2 + t] = db2;
-  }
   if (t < kMlpOut) P[kOffB3 + t] = red[t] + red[16 + t] + red[32 + t] + red[48 + t];
   if (t == 0) loss_part[blockIdx.x] = red[64] + red[65] + red[66] + red[67];
   if (!ok && t == 0) atomicAdd(err, 1u);
