@@ -271,12 +271,17 @@ int aton_set_pair_sink(aton_handle h, float* records, int64_t capacity, int stri
 int aton_pair_count(aton_handle h, int64_t* count);
 
 /* Uses network m in the chemistry of later steps (NULL or enabled = 0: off). The handle keeps
- * the pointer; m must outlive its use. Steps then run the plain path with the surrogate
- * chemistry kernel. A cell is offered to the network when its explicit sub-step estimate from
- * photo-ionisation and photo-heating is >= gate_substeps and its features lie in the training
- * range; a prediction is accepted when
- * its photons absorbed per atom match the atoms ionised plus the recombinations over dt within
- * residual_max of max(y, 1e-8); every other cell takes the exact operator. */
+ * the pointer; m must outlive its use. In ATON_MODE_FUSED with the GLF flux and nx a multiple
+ * of 4 the step stays one launch: the TMA-staged fused kernel lists the cells its gate selects
+ * (cells off the one-sub-step chemistry shortcut only) and runs the network for them at the end
+ * of each CTA; otherwise (ATON_MODE_UNFUSED, ATON_MODE_FUSED_LDG, the HLL flux, nx not a
+ * multiple of 4) the step runs the plain path with a gate pass and a surrogate pass
+ * (aton_launches_per_step reports which). A cell is offered to the network when its explicit
+ * sub-step estimate from photo-ionisation and photo-heating is >= gate_substeps and its features
+ * lie in the training range; a prediction is accepted when its photons absorbed per atom match
+ * the atoms ionised plus the recombinations over dt within residual_max of max(y, 1e-8); every
+ * other cell takes the exact operator. The first fused step after this call (or after a change
+ * of tile) allocates the per-tile lists (64 cells of 32 bytes per tile). */
 void aton_default_surrogate_params(aton_surrogate_params* p);
 int aton_set_surrogate(aton_handle h, aton_mlp_handle m, const aton_surrogate_params* p);
 
