@@ -112,7 +112,11 @@ inline bool standard_chemistry(const StepParams& P) {
 }
 
 // ---- training step of the surrogate MLP on tcgen05 (aton_mlp_tc.cu) ----
-__global__ void k_mlp_train_tc(const MlpImage* __restrict__ img, const float* __restrict__ X,
+// 128 rows per CTA of kMlpTcThreads threads; one partial gradient per CTA, kMlpPartStride floats
+// apart (the parameter vector padded to a multiple of four floats: 16-byte stores)
+constexpr int kMlpTcThreads = 256;
+constexpr int kMlpPartStride = (kMlpParams + 3) & ~3;
+__global__ void k_mlp_train_tc(const MlpTcImage* __restrict__ img, const float* __restrict__ X,
                                const float* __restrict__ T, int n, float inv_count, float* partial,
                                float* loss_part, unsigned int* err);
 size_t mlp_train_tc_smem();

@@ -48,26 +48,38 @@ __device__ __forceinline__ void copy_image(MlpImage* dst, const MlpImage* src, b
   }
 }
 
-// Places parameter p (value v) into the BF16 image (and its transposed copy).
-__device__ __forceinline__ void image_put(MlpImage* img, int p, float v) {
+// Places parameter p (value v) into the BF16 image (and its transposed copy) and into the
+// training kernel's canonical image.
+__device__ __forceinline__ void image_put(MlpImage* img, MlpTcImage* tc, int p, float v) {
   const __nv_bfloat16 b = __float2bfloat16(v);
+  auto tcw = [&](unsigned char* m, int r, int c, int P) {
+    *reinterpret_cast<__nv_bfloat16*>(m + tc_cano(r, c, P)) = b;
+  };
   if (p < kOffB1) {
     const int o = p / kMlpIn, i = p % kMlpIn;
     img->W1[o * kP1 + i] = b;
+    tcw(tc->W1, o, i, 16);
   } else if (p < kOffW2) {
     img->b1[p - kOffB1] = v;
+    tc->bias[p - kOffB1] = v;
   } else if (p < kOffB2) {
     const int q = p - kOffW2, o = q / kMlpH, i = q % kMlpH;
     img->W2[o * kP2 + i] = b;
     img->W2T[i * kP2 + o] = b;
+    tcw(tc->W2, o, i, 64);
+    tcw(tc->W2T, i, o, 64);
   } else if (p < kOffW3) {
     img->b2[p - kOffB2] = v;
+    tc->bias[64 + p - kOffB2] = v;
   } else if (p < kOffB3) {
     const int q = p - kOffW3, o = q / kMlpH, i = q % kMlpH;
     img->W3[o * kP2 + i] = b;
     img->W3T[i * kP3T + o] = b;
+    tcw(tc->W3, o, i, 64);
+    tcw(tc->W3T, i, o, 16);
   } else {
     img->b3[p - kOffB3] = v;
+    tc->bias[128 + p - kOffB3] = v;
   }
 }
 
@@ -75,11 +87,11 @@ __device__ __forceinline__ void image_put(MlpImage* img, int p, float v) {
 // weights and moments and refreshes the image; otherwise writes the gradient to `grad`.
 __global__ void k_mlp_adam(const float* __restrict__ partial, int nblk, float* theta, float* m,
                            float* v, float lr, float b1, float b2, float eps, float bc1, float bc2,
-                           MlpImage* img, float* grad, int adam) {
+                           MlpImage* img, MlpTcImage* tc, float* grad, int adam) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= kMlpParams) return;
   double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += (double)partial[(size_t)b * kMlpParams + p];
+  for (int b = 0; b < nblk; ++b) s += (double)partial[(size_t)b * kMlpPartStride + p];
   const float gr = (float)s;
   if (!adam) {
     grad[p] = gr;
@@ -91,7 +103,7 @@ __global__ void k_mlp_adam(const float* __restrict__ partial, int nblk, float* t
   v[p] = vv;
   const float th = theta[p] - lr * (mm / bc1) / (sqrtf(vv / bc2) + eps);
   theta[p] = th;
-  image_put(img, p, th);
+  image_put(img, tc, p, th);
 }
 
 __global__ void k_mlp_loss(const float* loss_part, int nblk, float inv_count, double* out) {
@@ -102,9 +114,9 @@ __global__ void k_mlp_loss(const float* loss_part, int nblk, float inv_count, do
   }
 }
 
-__global__ void k_mlp_image(const float* theta, MlpImage* img) {
+__global__ void k_mlp_image(const float* theta, MlpImage* img, MlpTcImage* tc) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < kMlpParams) image_put(img, p, theta[p]);
+  if (p < kMlpParams) image_put(img, tc, p, theta[p]);
 }
 
 // Deterministic initialisation: uniform in +-sqrt(6/fan_in) for weights (counter hash of the
@@ -258,6 +270,7 @@ struct aton_mlp {
   float* m = nullptr;
   float* v = nullptr;
   MlpImage* img = nullptr;
+  MlpTcImage* tcimg = nullptr;   // the training kernel's canonical copy of the weights
   MlpNorm* norm = nullptr;
   float* partial = nullptr;
   float* loss_part = nullptr;
@@ -289,7 +302,7 @@ static int ensure_blocks(aton_mlp* h, int nblk) {
   cudaFree(h->loss_part);
   h->partial = nullptr;
   h->loss_part = nullptr;
-  MCU(cudaMalloc(&h->partial, sizeof(float) * (size_t)nblk * kMlpParams));
+  MCU(cudaMalloc(&h->partial, sizeof(float) * (size_t)nblk * kMlpPartStride));
   MCU(cudaMalloc(&h->loss_part, sizeof(float) * nblk));
   h->cap_blocks = nblk;
   return ATON_OK;
@@ -308,6 +321,7 @@ int aton_mlp_create(aton_mlp_handle* out, unsigned long long seed) {
       cudaMalloc(&h->m, sizeof(float) * kMlpParams) != cudaSuccess ||
       cudaMalloc(&h->v, sizeof(float) * kMlpParams) != cudaSuccess ||
       cudaMalloc(&h->img, sizeof(MlpImage)) != cudaSuccess ||
+      cudaMalloc(&h->tcimg, sizeof(MlpTcImage)) != cudaSuccess ||
       cudaMalloc(&h->norm, sizeof(MlpNorm)) != cudaSuccess ||
       cudaMalloc(&h->d_loss, sizeof(double)) != cudaSuccess ||
       cudaMalloc(&h->d_acc, sizeof(double) * 16 * 148) != cudaSuccess ||
@@ -322,12 +336,13 @@ int aton_mlp_create(aton_mlp_handle* out, unsigned long long seed) {
   cudaMemsetAsync(h->m, 0, sizeof(float) * kMlpParams, s);
   cudaMemsetAsync(h->v, 0, sizeof(float) * kMlpParams, s);
   cudaMemsetAsync(h->img, 0, sizeof(MlpImage), s);   // padding stays zero
+  cudaMemsetAsync(h->tcimg, 0, sizeof(MlpTcImage), s);
   MlpNorm id{};
   for (int i = 0; i < kMlpIn; ++i) { id.in_scale[i] = 1.f; id.in_min[i] = -3e38f; id.in_max[i] = 3e38f; }
   for (int i = 0; i < kMlpOut; ++i) id.out_scale[i] = 1.f;
   cudaMemcpyAsync(h->norm, &id, sizeof(id), cudaMemcpyHostToDevice, s);
   k_mlp_init<<<(kMlpParams + 255) / 256, 256, 0, s>>>(h->theta, seed);
-  k_mlp_image<<<(kMlpParams + 255) / 256, 256, 0, s>>>(h->theta, h->img);
+  k_mlp_image<<<(kMlpParams + 255) / 256, 256, 0, s>>>(h->theta, h->img, h->tcimg);
   if (cudaStreamSynchronize(s) != cudaSuccess) return bail(mfail(ATON_ERR_CUDA, "init"));
   *out = h;
   return ATON_OK;
@@ -336,7 +351,8 @@ int aton_mlp_create(aton_mlp_handle* out, unsigned long long seed) {
 void aton_mlp_destroy(aton_mlp_handle h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
-  cudaFree(h->theta); cudaFree(h->m); cudaFree(h->v); cudaFree(h->img); cudaFree(h->norm);
+  cudaFree(h->theta); cudaFree(h->m); cudaFree(h->v); cudaFree(h->img); cudaFree(h->tcimg);
+  cudaFree(h->norm);
   cudaFree(h->partial); cudaFree(h->loss_part); cudaFree(h->d_loss); cudaFree(h->d_acc);
   cudaFree(h->d_mm); cudaFree(h->d_err);
   if (h->stream) cudaStreamDestroy(h->stream);
@@ -352,7 +368,7 @@ int aton_mlp_set_params(aton_mlp_handle h, const float* theta, int where) {
   MCU(cudaMemsetAsync(h->m, 0, sizeof(float) * kMlpParams, h->stream));
   MCU(cudaMemsetAsync(h->v, 0, sizeof(float) * kMlpParams, h->stream));
   h->step = 0;
-  k_mlp_image<<<(kMlpParams + 255) / 256, 256, 0, h->stream>>>(h->theta, h->img);
+  k_mlp_image<<<(kMlpParams + 255) / 256, 256, 0, h->stream>>>(h->theta, h->img, h->tcimg);
   MCU(cudaGetLastError());
   MCU(cudaStreamSynchronize(h->stream));
   return ATON_OK;
@@ -425,8 +441,8 @@ static int train_common(aton_mlp* h, const float* X, const float* T, int n, int 
   const int nblk = (n + kRows - 1) / kRows;
   if (int rc = ensure_blocks(h, nblk)) return rc;
   const float inv = 1.f / (float)((double)n * kMlpOut);
-  k_mlp_train_tc<<<nblk, 128, mlp_train_tc_smem(), h->stream>>>(h->img, X, T, n, inv, h->partial,
-                                                               h->loss_part, h->d_err);
+  k_mlp_train_tc<<<nblk, kMlpTcThreads, mlp_train_tc_smem(), h->stream>>>(
+      h->tcimg, X, T, n, inv, h->partial, h->loss_part, h->d_err);
   MCU(cudaGetLastError());
   float bc1 = 1.f, bc2 = 1.f;
   if (adam) {
@@ -436,7 +452,7 @@ static int train_common(aton_mlp* h, const float* X, const float* T, int n, int 
   }
   k_mlp_adam<<<(kMlpParams + 255) / 256, 256, 0, h->stream>>>(h->partial, nblk, h->theta, h->m,
                                                               h->v, lr, 0.9f, 0.999f, 1e-8f, bc1,
-                                                              bc2, h->img, grad, adam);
+                                                              bc2, h->img, h->tcimg, grad, adam);
   k_mlp_loss<<<1, 32, 0, h->stream>>>(h->loss_part, nblk, 1.0 / ((double)n * kMlpOut), h->d_loss);
   MCU(cudaGetLastError());
   if (loss) {

@@ -40,6 +40,26 @@ struct MlpImage {
 // transposed blocks only for training)
 constexpr size_t kImgBytes = sizeof(MlpImage);
 
+// Byte offset of element (r, c) of a [row][column] BF16 matrix of pitch P columns in the
+// canonical no-swizzle layout of the tcgen05 operands: 8 x 8 core matrices of 128 bytes (8 rows
+// of 16 bytes, a row's 8 consecutive columns), core matrices adjacent along the columns 128
+// bytes apart, 8-row groups P x 16 bytes apart.
+__host__ __device__ constexpr unsigned tc_cano(int r, int c, int P) {
+  return (unsigned)((r >> 3) * (P * 16) + (c >> 3) * 128 + (r & 7) * 16 + (c & 7) * 2);
+}
+
+// The training kernel's weight operands, byte for byte as they sit in its shared memory (one
+// bulk copy per CTA): each matrix [row][column] in the canonical layout, padding zero.
+struct MlpTcImage {
+  unsigned char W1[64 * 16 * 2];    // W1    [out][in]   64 x 16 (inputs 5..15 zero)
+  unsigned char W2[64 * 64 * 2];    // W2    [out][in]   64 x 64
+  unsigned char W3[16 * 64 * 2];    // W3    [out][in]   16 x 64 (outputs 3..15 zero)
+  unsigned char W2T[64 * 64 * 2];   // W2^T  [in][out]   64 x 64
+  unsigned char W3T[64 * 16 * 2];   // W3^T  [in][out]   64 x 16 (outputs 3..15 zero)
+  float bias[144];                  // b1 [0, 64), b2 [64, 128), b3 [128, 131)
+};
+static_assert(sizeof(MlpTcImage) % 16 == 0, "bulk copies move multiples of 16 bytes");
+
 // Ranges of the targets (changes of log10 y, log10 T, log10 N over one step), applied to the
 // training targets and to the decoded predictions alike.
 constexpr float kDlyMax = 6.f, kDlTMax = 3.f, kDlNMax = 6.f;

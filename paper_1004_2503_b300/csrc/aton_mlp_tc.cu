@@ -2,8 +2,11 @@
 // 5th-generation tensor cores (tcgen05): forward and backward of 128 rows per CTA with BF16
 // operands in shared memory and FP32 accumulators in tensor memory (TMEM).
 //
-// One CTA of 128 threads takes 128 rows; thread t owns row t, which is TMEM lane t in every
-// accumulator (M = 128, one row per lane). Thread 0 issues the products (tcgen05.mma,
+// One CTA of 256 threads takes 128 rows; row r is TMEM lane r of every accumulator (M = 128,
+// one row per lane). Warp w may read TMEM lanes 32 (w mod 4) .. +31, so warps w and w + 4 share
+// the rows of a lane quadrant and split the columns of each accumulator between them. Thread 0
+// brings the weight operands in with one bulk copy (they sit in device memory already in the
+// shared-memory layout, refreshed by every Adam step), issues the products (tcgen05.mma,
 // kind::f16, BF16 x BF16 -> FP32) and commits each group to an mbarrier; the threads read the
 // accumulators back with tcgen05.ld, apply the bias and the activation in registers and write
 // the next operands to shared memory, a row's 8 consecutive features as one 16-byte store.
@@ -38,9 +41,11 @@ namespace aton {
 
 namespace {
 
-constexpr int kTcRows = 128;          // rows per CTA = threads = TMEM lanes
+constexpr int kTcRows = 128;          // rows per CTA = TMEM lanes
+constexpr int kTcThreads = kMlpTcThreads;   // two warps per lane quadrant
 constexpr unsigned kTmemCols = 256;   // columns allocated (power of two >= 32)
 constexpr unsigned kWaitPolls = 1u << 24;
+static_assert(kTcThreads == 2 * kTcRows, "two threads per row");
 
 // shared-memory buffers (byte offsets; every block 1024-aligned), [row][feature] canonical
 constexpr int kPHX = 96;                             // HX: H1 0..63, X 64..79, 1 at 80, 0 81..95
@@ -49,23 +54,24 @@ constexpr uint32_t kSmHX = 0;
 constexpr uint32_t kSmH2 = kSmHX + 128 * kPHX * 2;
 constexpr uint32_t kSmDZ = kSmH2 + 128 * kPH2 * 2;
 constexpr uint32_t kSmDY = kSmDZ + 128 * kPDZ * 2;
-constexpr uint32_t kSmW1 = kSmDY + 128 * kPDY * 2;    // W1     64 x 16 (inputs 5..15 zero)
-constexpr uint32_t kSmW2 = kSmW1 + 64 * 16 * 2;       // W2     64 x 64
-constexpr uint32_t kSmW3 = kSmW2 + 64 * 64 * 2;       // W3     16 x 64 (outputs 3..15 zero)
-constexpr uint32_t kSmW2T = kSmW3 + 16 * 64 * 2;      // W2^T   64 x 64
-constexpr uint32_t kSmW3T = kSmW2T + 64 * 64 * 2;     // W3^T   64 x 16
-constexpr uint32_t kSmBias = kSmW3T + 64 * 16 * 2;    // b1[64], b2[64], b3[16] (FP32)
-constexpr uint32_t kSmRed = kSmBias + 144 * 4;        // per-warp dy sums [4][16], loss [4]
-constexpr uint32_t kSmBar = kSmRed + (4 * 16 + 4) * 4 + 8;   // mbarrier (8-aligned)
-constexpr uint32_t kSmTmem = kSmBar + 8;              // TMEM base written by tcgen05.alloc
-constexpr uint32_t kTcSmem = kSmTmem + 8 + 1024;      // (+ alignment slack of the base)
-static_assert(kSmBar % 8 == 0, "mbarrier alignment");
+constexpr uint32_t kSmW = kSmDY + 128 * kPDY * 2;     // the weight operands (an MlpTcImage)
+constexpr uint32_t kSmW1 = kSmW + offsetof(MlpTcImage, W1);
+constexpr uint32_t kSmW2 = kSmW + offsetof(MlpTcImage, W2);
+constexpr uint32_t kSmW3 = kSmW + offsetof(MlpTcImage, W3);
+constexpr uint32_t kSmW2T = kSmW + offsetof(MlpTcImage, W2T);
+constexpr uint32_t kSmW3T = kSmW + offsetof(MlpTcImage, W3T);
+constexpr uint32_t kSmBias = kSmW + offsetof(MlpTcImage, bias);   // b1[64], b2[64], b3[16]
+constexpr uint32_t kSmRed = kSmW + sizeof(MlpTcImage);   // per-warp dy sums [4][16], loss [4]
+constexpr uint32_t kSmBar = kSmRed + (4 * 16 + 4) * 4;   // mbarrier of the products
+constexpr uint32_t kSmWBar = kSmBar + 8;                 // mbarrier of the weight copy
+constexpr uint32_t kSmTmem = kSmWBar + 8;                // TMEM base written by tcgen05.alloc
+constexpr uint32_t kTcSmem = kSmTmem + 8 + 1024;         // (+ alignment slack of the base)
+static_assert(kSmW % 16 == 0 && sizeof(MlpTcImage) % 16 == 0, "bulk copy alignment");
+static_assert(kSmBar % 8 == 0 && kSmWBar % 8 == 0, "mbarrier alignment");
 static_assert(kSmDZ - kSmH2 + 128 * kPDZ * 2 >= 17280, "the M = 128 view of H2 stays in bounds");
 
 // byte offset of element (r, c) in a [row][feature] buffer of pitch P features (canonical)
-__device__ __forceinline__ uint32_t cano(int r, int c, int P) {
-  return (uint32_t)((r >> 3) * (P * 16) + (c >> 3) * 128 + (r & 7) * 16 + (c & 7) * 2);
-}
+__device__ __forceinline__ uint32_t cano(int r, int c, int P) { return tc_cano(r, c, P); }
 
 // shared-memory matrix descriptor, no swizzle, descriptor version 1: start address, leading
 // byte offset (between core matrices adjacent along the contraction) and stride byte offset
@@ -181,59 +187,60 @@ __device__ __forceinline__ void put8(unsigned char* sm, uint32_t off, const floa
   *reinterpret_cast<uint4*>(sm + off) = q;
 }
 
+// bulk copy (TMA engine) of `bytes` from global to shared memory, completion counted on `bar`
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
 }  // namespace
 
-__global__ void __launch_bounds__(kTcRows, 2)
-    k_mlp_train_tc(const MlpImage* __restrict__ img, const float* __restrict__ X,
+__global__ void __launch_bounds__(kTcThreads, 2)
+    k_mlp_train_tc(const MlpTcImage* __restrict__ img, const float* __restrict__ X,
                    const float* __restrict__ T, int n, float inv_count, float* partial,
                    float* loss_part, unsigned int* err) {
   extern __shared__ __align__(1024) unsigned char tc_raw[];
   unsigned char* sm = tc_raw + ((1024u - (su32(tc_raw) & 1023u)) & 1023u);
   const uint32_t sb = su32(sm);
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
-  const int row = blockIdx.x * kTcRows + t;
+  const int r = t & (kTcRows - 1);   // this thread's row (TMEM lane)
+  const int hf = t >> 7;             // which half of the accumulator columns it reads
+  const int row = blockIdx.x * kTcRows + r;
   const bool valid = row < n;
   float* bias = reinterpret_cast<float*>(sm + kSmBias);
   float* red = reinterpret_cast<float*>(sm + kSmRed);
-  const uint32_t bar = sb + kSmBar;
+  const uint32_t bar = sb + kSmBar, wbar = sb + kSmWBar;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kSmTmem);
 
-  // the weights in K-major layout (their rows the products' N rows), zero padding
-  for (int i = t; i < 64 * 16; i += kTcRows) {   // W1 (64 x 16), W3^T (64 x 16)
-    const int o = i >> 4, k = i & 15;
-    *reinterpret_cast<__nv_bfloat16*>(sm + kSmW1 + cano(o, k, 16)) = img->W1[o * kP1 + k];
-    *reinterpret_cast<__nv_bfloat16*>(sm + kSmW3T + cano(o, k, 16)) = img->W3T[o * kP3T + k];
+  if (t == 0) {   // the weight operands: one bulk copy, already in the shared-memory layout
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(wbar));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    bulk_load(sb + kSmW, img, (uint32_t)sizeof(MlpTcImage), wbar);
   }
-  for (int i = t; i < 64 * 64; i += kTcRows) {   // W2, W2^T (64 x 64)
-    const int o = i >> 6, k = i & 63;
-    *reinterpret_cast<__nv_bfloat16*>(sm + kSmW2 + cano(o, k, 64)) = img->W2[o * kP2 + k];
-    *reinterpret_cast<__nv_bfloat16*>(sm + kSmW2T + cano(o, k, 64)) = img->W2T[o * kP2 + k];
-  }
-  for (int i = t; i < 16 * 64; i += kTcRows) {   // W3 (16 x 64; the image holds 8 rows)
-    const int o = i >> 6, k = i & 63;
-    const __nv_bfloat16 v = o < 8 ? img->W3[o * kP2 + k] : __float2bfloat16(0.f);
-    *reinterpret_cast<__nv_bfloat16*>(sm + kSmW3 + cano(o, k, 64)) = v;
-  }
-  for (int i = t; i < 144; i += kTcRows)
-    bias[i] = i < 64 ? img->b1[i] : (i < 128 ? img->b2[i - 64] : img->b3[i - 128]);
-  // this row's input into HX features 64..79 (5 used), the column of ones (80) and zeros
-  {
+  float tg[kMlpOut];
+  if (hf == 0) {   // this row's input into HX features 64..79 (5 used); its targets
     float v[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) v[k] = valid && k < kMlpIn ? X[(size_t)row * kMlpIn + k] : 0.f;
-    put8(sm, kSmHX + cano(t, 64, kPHX), v);
-    put8(sm, kSmHX + cano(t, 72, kPHX), v + 8);
+    put8(sm, kSmHX + cano(r, 64, kPHX), v);
+    put8(sm, kSmHX + cano(r, 72, kPHX), v + 8);
+#pragma unroll
+    for (int k = 0; k < kMlpOut; ++k) tg[k] = valid ? T[(size_t)row * kMlpOut + k] : 0.f;
+  } else {         // the column of ones (80) and zeros (81..95)
+    float v[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) v[k] = k == 0 ? 1.f : 0.f;
-    put8(sm, kSmHX + cano(t, 80, kPHX), v);
-    put8(sm, kSmHX + cano(t, 88, kPHX), v + 8);
-  }
-  float tg[kMlpOut];
+    put8(sm, kSmHX + cano(r, 80, kPHX), v);
+    put8(sm, kSmHX + cano(r, 88, kPHX), v + 8);
 #pragma unroll
-  for (int k = 0; k < kMlpOut; ++k) tg[k] = valid ? T[(size_t)row * kMlpOut + k] : 0.f;
-  if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int k = 0; k < kMlpOut; ++k) tg[k] = 0.f;
   }
   if (w == 0) {   // TMEM: 256 columns x 128 lanes of FP32
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -246,12 +253,13 @@ __global__ void __launch_bounds__(kTcRows, 2)
   fence_before();
   __syncthreads();
   fence_after();
+  const bool wok = bar_wait(wbar, 0);   // the weights have landed
+  bool ok = wok;
   const uint32_t tm = *tmem_slot;
-  const uint32_t lane_base = tm + ((uint32_t)(32 * w) << 16);   // this warp's TMEM lanes
+  const uint32_t lane_base = tm + ((uint32_t)(32 * (w & 3)) << 16);   // this warp's TMEM lanes
   // TMEM columns: Z1 [0, 64), Z2 then dH1 [64, 128), Y [128, 144), dH2 [144, 208);
   // afterwards the weight products: D' [0, 96), D'' [128, 144)
   const uint32_t cZ1 = 0, cZ2 = 64, cY = 128, cH2 = 144;
-  bool ok = true;
   uint32_t phase = 0;
   // issue (thread 0) a group of products and wait for it (every thread)
   auto run = [&](auto issue) {
@@ -271,75 +279,78 @@ __global__ void __launch_bounds__(kTcRows, 2)
     __syncthreads();
   };
   float z[16], g[16], v[16];
+  const int c0 = 32 * hf;   // this thread's 32 of the 64 hidden columns
 
   // ---- layer 1: Z1 = X W1^T
   run([&] { gemm_k(tm + cZ1, sb + kSmHX + 8 * 128, kPHX, sb + kSmW1, 16, 16, idesc(128, 64)); });
-  for (int c = 0; c < 64; c += 16) {
+  for (int c = c0; c < c0 + 32; c += 16) {
     tld16(lane_base + cZ1 + c, z);
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = silu(z[j] + bias[c + j]);
-    put8(sm, kSmHX + cano(t, c, kPHX), v);
-    put8(sm, kSmHX + cano(t, c + 8, kPHX), v + 8);
+    put8(sm, kSmHX + cano(r, c, kPHX), v);
+    put8(sm, kSmHX + cano(r, c + 8, kPHX), v + 8);
   }
   handoff();
   // ---- layer 2: Z2 = H1 W2^T
   run([&] { gemm_k(tm + cZ2, sb + kSmHX, kPHX, sb + kSmW2, 64, 64, idesc(128, 64)); });
-  for (int c = 0; c < 64; c += 16) {
+  for (int c = c0; c < c0 + 32; c += 16) {
     tld16(lane_base + cZ2 + c, z);
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = silu(z[j] + bias[64 + c + j]);
-    put8(sm, kSmH2 + cano(t, c, kPH2), v);
-    put8(sm, kSmH2 + cano(t, c + 8, kPH2), v + 8);
+    put8(sm, kSmH2 + cano(r, c, kPH2), v);
+    put8(sm, kSmH2 + cano(r, c + 8, kPH2), v + 8);
   }
   handoff();
-  // ---- layer 3: Y = H2 W3^T + b3; dY = 2 (Y - T) / (rows x 3); the loss
+  // ---- layer 3: Y = H2 W3^T + b3; dY = 2 (Y - T) / (rows x 3); the loss (first half only)
   run([&] { gemm_k(tm + cY, sb + kSmH2, kPH2, sb + kSmW3, 64, 64, idesc(128, 16)); });
-  float dy[kMlpOut], sq = 0.f;
-  tld16(lane_base + cY, z);
+  if (hf == 0) {
+    float dy[kMlpOut], sq = 0.f;
+    tld16(lane_base + cY, z);
 #pragma unroll
-  for (int k = 0; k < kMlpOut; ++k) {
-    const float d = valid ? z[k] + bias[128 + k] - tg[k] : 0.f;
-    dy[k] = 2.f * d * inv_count;
-    sq += d * d;
+    for (int k = 0; k < kMlpOut; ++k) {
+      const float d = valid ? z[k] + bias[128 + k] - tg[k] : 0.f;
+      dy[k] = 2.f * d * inv_count;
+      sq += d * d;
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = k < kMlpOut ? dy[k] : 0.f;
+    put8(sm, kSmDY + cano(r, 0, kPDY), v);
+    put8(sm, kSmDY + cano(r, 8, kPDY), v + 8);
+    // per-warp sums of dy (db3) and of the squared error, in lane order
+#pragma unroll
+    for (int k = 0; k < kMlpOut; ++k) {
+      float s = dy[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) red[w * 16 + k] = s;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if (lane == 0) red[64 + w] = sq;
   }
-#pragma unroll
-  for (int k = 0; k < 16; ++k) v[k] = k < kMlpOut ? dy[k] : 0.f;
-  put8(sm, kSmDY + cano(t, 0, kPDY), v);
-  put8(sm, kSmDY + cano(t, 8, kPDY), v + 8);
-  // per-warp sums of dy (db3) and of the squared error, in lane order
-#pragma unroll
-  for (int k = 0; k < kMlpOut; ++k) {
-    float s = dy[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) red[w * 16 + k] = s;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-  if (lane == 0) red[64 + w] = sq;
   handoff();
   // ---- dH2 = dY W3 (B = W3^T, K = 16 outputs)
   run([&] { gemm_k(tm + cH2, sb + kSmDY, kPDY, sb + kSmW3T, 16, 16, idesc(128, 64)); });
   // dZ2 = dH2 * silu'(Z2 + b2) into DZ features 0..63
-  for (int c = 0; c < 64; c += 16) {
+  for (int c = c0; c < c0 + 32; c += 16) {
     tld16(lane_base + cZ2 + c, z);
     tld16(lane_base + cH2 + c, g);
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = g[j] * dsilu(z[j] + bias[64 + c + j]);
-    put8(sm, kSmDZ + cano(t, c, kPDZ), v);
-    put8(sm, kSmDZ + cano(t, c + 8, kPDZ), v + 8);
+    put8(sm, kSmDZ + cano(r, c, kPDZ), v);
+    put8(sm, kSmDZ + cano(r, c + 8, kPDZ), v + 8);
   }
   handoff();
   // ---- dH1 = dZ2 W2 (B = W2^T, K = 64) into the columns of Z2
   run([&] { gemm_k(tm + cZ2, sb + kSmDZ, kPDZ, sb + kSmW2T, 64, 64, idesc(128, 64)); });
   // dZ1 = dH1 * silu'(Z1 + b1) into DZ features 64..127
-  for (int c = 0; c < 64; c += 16) {
+  for (int c = c0; c < c0 + 32; c += 16) {
     tld16(lane_base + cZ1 + c, z);
     tld16(lane_base + cZ2 + c, g);
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = g[j] * dsilu(z[j] + bias[c + j]);
-    put8(sm, kSmDZ + cano(t, 64 + c, kPDZ), v);
-    put8(sm, kSmDZ + cano(t, 64 + c + 8, kPDZ), v + 8);
+    put8(sm, kSmDZ + cano(r, 64 + c, kPDZ), v);
+    put8(sm, kSmDZ + cano(r, 64 + c + 8, kPDZ), v + 8);
   }
   handoff();
   // ---- weight and bias gradients over the rows: [dZ2 | dZ1]^T [H1 | X | 1], H2^T dY
@@ -347,26 +358,41 @@ __global__ void __launch_bounds__(kTcRows, 2)
     gemm_mn(tm + 0, sb + kSmDZ, kPDZ, sb + kSmHX, kPHX, idesc(128, 96, true, true));
     gemm_mn(tm + cY, sb + kSmH2, kPH2, sb + kSmDY, kPDY, idesc(128, 16, true, true));
   });
-  float* P = partial + (size_t)blockIdx.x * kMlpParams;
-  for (int c = 0; c < 96; c += 16) {
+  float* P = partial + (size_t)blockIdx.x * kMlpPartStride;
+  // D' columns: the first half reads 0..47, the second 48..95; lane r < 64 holds row r of dW2
+  // (columns 0..63, 16-byte stores), lane r >= 64 row r - 64 of dW1 (columns 64..68); column 80
+  // holds db2 (r < 64) and db1 (r >= 64)
+  for (int c = 48 * hf; c < 48 * hf + 48; c += 16) {
     tld16(lane_base + c, z);
+    if (!ok)
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      const int col = c + j;
-      const float val = ok ? z[j] : 0.f;
-      if (t < 64 && col < 64) P[kOffW2 + t * kMlpH + col] = val;                  // dW2[t][col]
-      if (t >= 64 && col >= 64 && col - 64 < kMlpIn)
-        P[kOffW1 + (t - 64) * kMlpIn + (col - 64)] = val;                          // dW1
-      if (col == 80) P[t < 64 ? kOffB2 + t : kOffB1 + (t - 64)] = val;            // db2, db1
+      for (int j = 0; j < 16; ++j) z[j] = 0.f;
+    if (c < 64) {
+      if (r < 64)
+#pragma unroll
+        for (int j = 0; j < 16; j += 4)
+          *reinterpret_cast<float4*>(P + kOffW2 + r * kMlpH + c + j) =
+              make_float4(z[j], z[j + 1], z[j + 2], z[j + 3]);
+    } else if (c == 64) {
+      if (r >= 64)
+#pragma unroll
+        for (int j = 0; j < kMlpIn; ++j) P[kOffW1 + (r - 64) * kMlpIn + j] = z[j];
+    } else {   // c == 80
+      P[r < 64 ? kOffB2 + r : kOffB1 + (r - 64)] = z[0];
     }
   }
-  tld16(lane_base + cY, z);
-  if (t < 64)
+  if (hf == 1) {   // D'': dW3[k][r] for r < 64
+    tld16(lane_base + cY, z);
+    if (r < 64)
 #pragma unroll
-    for (int k = 0; k < kMlpOut; ++k) P[kOffW3 + k * kMlpH + t] = ok ? z[k] : 0.f;   // dW3[k][t]
+      for (int k = 0; k < kMlpOut; ++k) P[kOffW3 + k * kMlpH + r] = ok ? z[k] : 0.f;
+  }
   if (t < kMlpOut) P[kOffB3 + t] = red[t] + red[16 + t] + red[32 + t] + red[48 + t];
   if (t == 0) loss_part[blockIdx.x] = red[64] + red[65] + red[66] + red[67];
   if (!ok && t == 0) atomicAdd(err, 1u);
+  // if the weight copy did not complete in time, wait (bounded) once more before the CTA exits,
+  // so that the copy does not write into shared memory afterwards
+  if (!wok && t == 0) bar_wait(wbar, 0);
   fence_before();
   __syncthreads();
   if (w == 0) {

@@ -6,7 +6,7 @@ namespace aton {
 
 constexpr int kStatsMaxBins = 64;          // per histogram axis (ATON_STATS_MAX_BINS)
 constexpr int kStatsThreads = 256;
-constexpr int kStatsBlocks = 148 * 5;      // fixed grid (five CTAs per SM): fixed summation order
+constexpr int kStatsBlocks = 148 * 3;      // fixed grid (three CTAs per SM): fixed summation order
 constexpr int kStatsScalars = 7;           // sums of y, nH, nH y, N, T, nH T, N on the plateau
 
 struct StatsArgs {

@@ -32,7 +32,8 @@ def _compare(a, st, run, **params):
     return got, ref
 
 
-@pytest.mark.parametrize("shape", [(20, 24, 36), (7, 5, 3), (33, 17, 9)])
+# cell counts 17280, 105, 5049, 175 and 18: every remainder modulo the four cells a thread takes
+@pytest.mark.parametrize("shape", [(20, 24, 36), (7, 5, 3), (33, 17, 9), (5, 5, 7), (3, 2, 3)])
 def test_stats_match_the_reference_on_an_evolved_box(shape):
     st, idx, rate, run = W.workload_small(shape=shape, nsrc=3)
     a = A.from_workload(st, idx, rate, run)
@@ -41,6 +42,10 @@ def test_stats_match_the_reference_on_an_evolved_box(shape):
     # a narrower, finer binning with a different spectral reading and plateau
     _compare(a, st, run, nb_nH=64, nb_y=7, nb_J=33, nH_lo=1e-5, nH_hi=1e-2, y_lo=1e-5,
              J21_lo=1e-3, J21_hi=1e2, spectral_index=0.0, nH_plateau=1e-4)
+    # the pass sums in a fixed order: a second call gives the same bits
+    again = a.ionisation_stats()
+    for k in SCALARS:
+        assert again[k] == got[k], k
     a.close()
     assert got["hist_y"].sum() == np.prod(shape)
 
