@@ -203,7 +203,8 @@ __global__ void __launch_bounds__(kStatsThreads, kStatsBlocks / 148) k_stats(con
     for (int k = 0; k < kBands; ++k) {
       const int i = bb * kBands + k;
       const unsigned long long a = ((unsigned long long)S.Ahi[q][i] << 32) | S.Alo[q][i];
-      r += ldexp((double)a, 8 * k - 150);
+      // a 2^(8k - 150): the power of two built from its bit pattern (a normal double)
+      if (a) r += (double)a * __longlong_as_double((long long)(1023 + 8 * k - 150) << 52);
     }
     pb[t] = (S.bad[q] >> bb) & 1ull ? __longlong_as_double(0x7FF8000000000000ll) : r;
   }
@@ -223,13 +224,16 @@ __global__ void __launch_bounds__(kStatsThreads, kStatsBlocks / 148) k_stats(con
 __global__ void k_stats_final(const double* part_scalar, const double* part_bins, int nblocks,
                               double* out) {
   const int t = threadIdx.x;
+  // (the loads are unrolled ahead of the additions, which stay in slot order)
   if (t < kStatsScalars) {
     double r = 0.0;
+#pragma unroll 16
     for (int b = 0; b < nblocks; ++b) r += part_scalar[(size_t)b * kStatsScalars + t];
     out[t] = r;
   } else if (t < kStatsScalars + 2 * kMB) {
     const int k = t - kStatsScalars;
     double r = 0.0;
+#pragma unroll 16
     for (int b = 0; b < nblocks; ++b) r += part_bins[(size_t)b * kMB * 2 + k];
     out[t] = r;
   }
