@@ -322,12 +322,15 @@ def ours(args, world, rank, local):
     if args.tile:
         ty, tz = (int(v) for v in args.tile.split(","))
         a.set_tile(ty, tz)
+        if args.rows:
+            a.set_tile_rows(args.rows)
         tune_ms = None
         a.set_exec({"tma": A.MODE_FUSED, "ldg": A.MODE_FUSED_LDG}.get(args.kernel, A.MODE_FUSED),
                    args.graph_batch)
     else:
         ty, tz, tune_ms = a.autotune(3)
     fused_mode = a.get_exec()["mode"]
+    args.tile_rows = a.get_tile_rows()
     kernel = "k_fused_tma" if fused_mode == A.MODE_FUSED else "k_fused"
     a.set_exec(fused_mode, args.graph_batch)
     sur_info = None
@@ -434,6 +437,7 @@ def ours(args, world, rank, local):
     b.set_params(bc=A.BC_PERIODIC, sigma_n=run["sigma_n"], sigma_e=run["sigma_e"],
                  e_gamma_eV=run["e_gamma_eV"], flux=flux)
     b.set_tile(ty, tz)
+    b.set_tile_rows(args.tile_rows)
     b.set_exec(fused_mode, args.graph_batch)
     b.set_fields(pin["N"], pin["Fx"], pin["Fy"], pin["Fz"], pin["T"], pin["nH"], y=ypin)
     b.add_sources(idx, rate)
@@ -480,7 +484,7 @@ def finish(args, world, rank, dist, st, idx, rate, run, desc, ncell, value, ms, 
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "grid": args.grid, "cells": ncell, "sources": len(idx),
                    "mode": kernel, "flux": args.flux, "graph_batch": args.graph_batch,
-                   "tile_ty_tz": [ty, tz],
+                   "tile_ty_tz": [ty, tz], "tile_rows_per_thread": getattr(args, "tile_rows", None),
                    "autotune_ms_per_step": tune_ms, "parallelism": f"replicas x{world}",
                    "l2": f"no flush: {44 * ncell / 1e9:.1f} GB of state per step >> 126 MB L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -534,6 +538,8 @@ def main():
     ap.add_argument("--with-surrogate", action="store_true",
                     help="run the timed steps with the chemistry surrogate in the fused kernel")
     ap.add_argument("--tile", default="", help="TY,TZ of the fused kernel (skips the autotuner)")
+    ap.add_argument("--rows", type=int, default=0,
+                    help="rows of the fused tile per thread (1 or 2; with --tile)")
     ap.add_argument("--flux", default="glf", choices=["glf", "hll"],
                     help="intercell flux: global Lax-Friedrichs (the paper's) or HLL")
     ap.add_argument("--kernel", default="tma", choices=["tma", "ldg"],

@@ -158,8 +158,18 @@ int aton_get_exec(aton_handle h, int* mode, int* graph_batch, int* ty, int* tz);
  * ty in {4, 8, 16}; tz >= 1. */
 int aton_set_tile(aton_handle h, int ty, int tz);
 
+/* Rows of the fused tile per thread (1 or 2; default 2). With 2, a CTA of ty/2 warps updates
+ * the same 32 x ty tile, each thread two neighbouring rows, which spreads the per-plane work
+ * that does not grow with the cells (stage wait, barrier, loop) and the halo rows over more
+ * cells. It applies to the TMA-staged kernel at tile heights 8 and 16 with the GLF flux;
+ * elsewhere the step runs one row per thread. aton_autotune chooses it with the tile. The
+ * fields do not depend on it beyond floating-point contraction (separately compiled kernels). */
+int aton_set_tile_rows(aton_handle h, int rows);
+int aton_get_tile_rows(aton_handle h, int* rows);
+
 /* Times the fused kernels (TMA-staged where the grid allows it, and plain-load) on a scratch
- * copy of the current state for each candidate tile and keeps the fastest kernel and tile (the
+ * copy of the current state for each candidate tile (and, for the TMA-staged kernel, one or two
+ * rows per thread) and keeps the fastest kernel and tile (the
  * simulation state is not advanced; an unfused mode stays unfused). `steps` per candidate
  * (>= 1). Writes the chosen (ty, tz) and its time per step [ms] when the pointers are not NULL;
  * aton_get_exec reports the chosen mode. */

@@ -26,7 +26,8 @@ BUDGET_KEYS = ("emitted", "stored", "absorbed", "escaped", "clipped", "stored0")
 # every entry point declared in include/aton.h
 EXPORTS = (
     "aton_default_params", "aton_init", "aton_finalize", "aton_set_params", "aton_get_params",
-    "aton_set_stream", "aton_set_exec", "aton_get_exec", "aton_set_tile", "aton_autotune", "aton_set_fields",
+    "aton_set_stream", "aton_set_exec", "aton_get_exec", "aton_set_tile", "aton_set_tile_rows",
+    "aton_get_tile_rows", "aton_autotune", "aton_set_fields",
     "aton_get_fields", "aton_add_sources", "aton_step", "aton_synchronize",
     "aton_photon_budget", "aton_set_budget", "aton_get_diag", "aton_last_error_cells",
     "aton_launches_per_step", "aton_strerror", "aton_last_message", "aton_photon_sum_static",
@@ -117,6 +118,8 @@ def load():
     L.aton_set_stream.argtypes = [_VP, _VP]
     L.aton_set_exec.argtypes = [_VP, C.c_int, C.c_int]
     L.aton_set_tile.argtypes = [_VP, C.c_int, C.c_int]
+    L.aton_set_tile_rows.argtypes = [_VP, C.c_int]
+    L.aton_get_tile_rows.argtypes = [_VP, C.POINTER(C.c_int)]
     L.aton_get_exec.argtypes = [_VP] + [C.POINTER(C.c_int)] * 4
     L.aton_autotune.argtypes = [_VP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                 C.POINTER(C.c_float)]
@@ -269,6 +272,14 @@ class Aton:
 
     def set_tile(self, ty, tz):
         _check(self.L.aton_set_tile(self.h, int(ty), int(tz)), "aton_set_tile")
+
+    def set_tile_rows(self, rows):
+        _check(self.L.aton_set_tile_rows(self.h, int(rows)), "aton_set_tile_rows")
+
+    def get_tile_rows(self):
+        r = C.c_int()
+        _check(self.L.aton_get_tile_rows(self.h, C.byref(r)), "aton_get_tile_rows")
+        return r.value
 
     def autotune(self, steps=3):
         ty, tz, ms = C.c_int(), C.c_int(), C.c_float()

@@ -95,6 +95,7 @@ struct aton_ctx {
   int mode = ATON_MODE_FUSED;
   int graph_batch = 100;
   int ty = 8, tz = 64;
+  int rpt = 2;         // rows of the fused tile per thread (2: TMA kernel, ty >= 8, GLF flux)
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
   TmaMaps tma[3];          // tile heights 4, 8, 16
   bool tma_ok[3] = {false, false, false};
@@ -378,9 +379,11 @@ static int enqueue_step(aton_handle h, cudaStream_t s) {
       a.sur.resid = (float)h->sur_p.residual_max;
       a.sur.buf = h->sur_buf;
       a.sur.cnt = h->sur_cnt;
-      e = launch_fused_tma(h->ty, a, h->tma[ti], s);
+      e = launch_fused_tma(h->ty, h->ty >= 8 ? h->rpt : 1, a, h->tma[ti], s);
     } else if (h->mode == ATON_MODE_FUSED && h->tma_ok[ti]) {
-      e = launch_fused_tma(h->ty, a, h->tma[ti], s);
+      // (two rows per thread: tile heights 8 and 16 with the GLF flux)
+      const int rpt = h->ty >= 8 && h->prm.flux != ATON_FLUX_HLL ? h->rpt : 1;
+      e = launch_fused_tma(h->ty, rpt, a, h->tma[ti], s);
     } else {
       e = launch_fused(h->ty, a, s);
     }
@@ -787,6 +790,22 @@ int aton_set_tile(aton_handle h, int ty, int tz) {
   return ATON_OK;
 }
 
+int aton_set_tile_rows(aton_handle h, int rows) {
+  if (int rc = check_h(h)) return rc;
+  if (rows != 1 && rows != 2) return fail(ATON_ERR_BADARG, "rows per thread must be 1 or 2");
+  if (rows == h->rpt) return ATON_OK;
+  h->rpt = rows;
+  drop_graphs(h);
+  return ATON_OK;
+}
+
+int aton_get_tile_rows(aton_handle h, int* rows) {
+  if (int rc = check_h(h)) return rc;
+  if (!rows) return fail(ATON_ERR_BADARG, "NULL rows");
+  *rows = h->rpt;
+  return ATON_OK;
+}
+
 int aton_set_fields(aton_handle h, const float* N, const float* Fx, const float* Fy,
                     const float* Fz, const float* x, const float* y, const float* T,
                     const float* nH, int where) {
@@ -1159,6 +1178,7 @@ int aton_autotune(aton_handle h, int steps, int* ty_out, int* tz_out, float* ms_
     CU(cudaMemcpyAsync(save[q], src[q], fb, cudaMemcpyDeviceToDevice, s));
   }
   const int mode0 = h->mode, gb0 = h->graph_batch, ty0 = h->ty, tz0 = h->tz, cur0 = h->cur;
+  const int rpt0 = h->rpt;
   h->graph_batch = 0;
   int best_ty = ty0, best_tz = tz0;
   float best = 1e30f;
@@ -1166,19 +1186,23 @@ int aton_autotune(aton_handle h, int steps, int* ty_out, int* tz_out, float* ms_
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
   const int tys[3] = {4, 8, 16};
-  const int tzs[5] = {16, 32, 64, 128, 256};
-  int best_mode = ATON_MODE_FUSED;
+  const int tzs[7] = {16, 32, 48, 64, 96, 128, 256};
+  int best_mode = ATON_MODE_FUSED, best_rpt = rpt0;
   int rc = ATON_OK;
   for (int kind = 0; kind < 2 && rc == ATON_OK; ++kind)
   for (int a = 0; a < 3 && rc == ATON_OK; ++a)
-    for (int b = 0; b < 5 && rc == ATON_OK; ++b) {
+  for (int rows = 1; rows <= 2 && rc == ATON_OK; ++rows)
+    for (int b = 0; b < 7 && rc == ATON_OK; ++b) {
       const int tz = std::min(tzs[b], h->nz);
       if (b > 0 && tz == std::min(tzs[b - 1], h->nz)) continue;
-      // kind 0: the TMA-staged kernel (when the grid allows it), kind 1: plain loads
+      // kind 0: the TMA-staged kernel (when the grid allows it), kind 1: plain loads; two rows
+      // per thread with the TMA-staged kernel at tile heights 8 and 16 and the GLF flux
       if (kind == 0 && !h->tma_ok[ty_index(tys[a])]) continue;
+      if (rows == 2 && (kind != 0 || tys[a] < 8 || h->prm.flux == ATON_FLUX_HLL)) continue;
       h->mode = kind == 0 ? ATON_MODE_FUSED : ATON_MODE_FUSED_LDG;
       h->ty = tys[a];
       h->tz = tz;
+      h->rpt = rows;
       h->tiles_dirty = true;
       if ((rc = prepare(h))) break;
       for (int q = 0; q < 6; ++q) {
@@ -1194,7 +1218,9 @@ int aton_autotune(aton_handle h, int steps, int* ty_out, int* tz_out, float* ms_
       float ms = 0;
       cudaEventElapsedTime(&ms, e0, e1);
       ms /= steps;
-      if (ms < best) { best = ms; best_ty = h->ty; best_tz = h->tz; best_mode = h->mode; }
+      if (ms < best) {
+        best = ms; best_ty = h->ty; best_tz = h->tz; best_mode = h->mode; best_rpt = h->rpt;
+      }
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1219,6 +1245,7 @@ int aton_autotune(aton_handle h, int steps, int* ty_out, int* tz_out, float* ms_
   h->graph_batch = gb0;
   h->ty = best_ty;
   h->tz = best_tz;
+  h->rpt = best_rpt;
   h->tiles_dirty = true;
   drop_graphs(h);
   if (rc) return rc;

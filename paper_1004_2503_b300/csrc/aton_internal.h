@@ -127,7 +127,8 @@ void set_last_message(const char* msg);
 // ---- launchers (aton_kernels.cu) ----
 cudaError_t init_kernel_attributes();
 cudaError_t init_tma_attributes();
-cudaError_t launch_fused_tma(int ty, const FusedArgs& a, const TmaMaps& m, cudaStream_t s);
+cudaError_t launch_fused_tma(int ty, int rpt, const FusedArgs& a, const TmaMaps& m,
+                             cudaStream_t s);
 bool make_tma_maps(int nx, int ny, int nz, int ty, float* const u[2][4], TmaMaps* out);
 cudaError_t launch_fused(int ty, const FusedArgs& a, cudaStream_t s);
 int fused_tiles(int nx, int ny, int nz, int ty, int tz);

@@ -108,12 +108,16 @@ struct Layout {
 // instead of global Lax-Friedrichs (the ring then also holds each cell's speed bounds). SUR:
 // the chemistry surrogate; a cell the gate selects (off the one-sub-step shortcut) is listed in
 // the CTA's region of a device buffer and, after the z-loop, runs through the network (sur_tail),
-// the accepted predictions replacing the exact operator.
-template <int TY, bool PER, bool STD, bool FULL, bool HLL = false, bool SUR = false>
-__global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
-                                                           const __grid_constant__ TmaMaps M) {
+// the accepted predictions replacing the exact operator. RPT: rows of the tile per thread (the
+// CTA has TY / RPT warps; thread row t owns the rows t RPT .. t RPT + RPT - 1), which spreads
+// the per-plane work that does not depend on the cell count (the stage wait, the barrier, the
+// loop) and the halo rows over more cells.
+template <int TY, bool PER, bool STD, bool FULL, bool HLL = false, bool SUR = false, int RPT = 1>
+__global__ void __launch_bounds__(kTileX * TY / RPT) k_fused_tma(const FusedArgs A,
+                                                                 const __grid_constant__ TmaMaps M) {
   using L = Layout<TY, HLL>;
-  constexpr int TX = kTileX, NH = 2 * TX + 2 * TY;
+  constexpr int TX = kTileX, NH = 2 * TX + 2 * TY, TYT = TY / RPT;
+  static_assert(TY % RPT == 0 && TX * TYT >= NH, "one halo slot per thread at most");
   extern __shared__ __align__(128) float sm_raw[];
   // 128-byte aligned base for the TMA boxes, as an offset from the shared array (so every
   // access below stays a shared-memory access)
@@ -129,7 +133,7 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
   unsigned long long* full = reinterpret_cast<unsigned long long*>(SZ + (HLL ? 3 * L::PLR : 0));
 
   const StepParams& P = A.P;
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + TX * ty;
+  const int tx = threadIdx.x, tid = tx + TX * threadIdx.y;
   const int nx = P.nx, ny = P.ny, nz = P.nz;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * A.tz;
   const int z1 = min(z0 + A.tz, nz);
@@ -162,10 +166,22 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
   __syncthreads();
 
   Tally tl;
-  const int gx = x0 + tx, gy = y0 + ty;
-  const bool act = FULL || (gx < nx && gy < ny);
-  const int oslot = (ty + 1) * kBoxX + (tx + 4);       // stage slot
-  const int orslot = (ty + 1) * L::RX + (tx + 1);      // ring slot
+  const int gx = x0 + tx;
+  // the thread's own rows ty = threadIdx.y RPT + r
+  bool act[RPT], own_out[RPT];
+  int oslot[RPT], orslot[RPT], gy[RPT], ocell[RPT];
+  long long ocol[RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    const int ty = threadIdx.y * RPT + r;
+    gy[r] = y0 + ty;
+    act[r] = FULL || (gx < nx && gy[r] < ny);
+    own_out[r] = !act[r];   // (false when FULL)
+    oslot[r] = (ty + 1) * kBoxX + (tx + 4);       // stage slot
+    orslot[r] = (ty + 1) * L::RX + (tx + 1);      // ring slot
+    ocell[r] = tx + TX * ty;                      // cell index in the tile (source lists)
+    ocol[r] = bc_map(gx, nx, PER) + (long long)nx * bc_map(gy[r], ny, PER);
+  }
   // halo slot of this thread (if any) in tile coordinates
   int hx = 0, hy = 0, hslot = -1, hrslot = -1;
   if (tid < NH) {
@@ -176,9 +192,7 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
     hslot = (hy + 1) * kBoxX + (hx + 4);
     hrslot = (hy + 1) * L::RX + (hx + 1);
   }
-  const bool own_out = !act;   // (false when FULL)
   const bool halo_out = hslot >= 0 && (x0 + hx < 0 || x0 + hx >= nx || y0 + hy < 0 || y0 + hy >= ny);
-  const long long ocol = bc_map(gx, nx, PER) + (long long)nx * bc_map(gy, ny, PER);
   const long long hcol = hslot >= 0 ? bc_map(x0 + hx, nx, PER) + (long long)nx * bc_map(y0 + hy, ny, PER) : 0;
   const float rc = P.rc, lam = P.lam;
   const float hl = 0.5f * lam, cu = 1.f - 3.f * lam;
@@ -223,23 +237,30 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
     }
   };
 
-  // plane z0-1 (own slot only) into ring plane 0, plane z0 into ring plane 1
+  // plane z0-1 (own slots only) into ring plane 0, plane z0 into ring plane 1
   wait(0);
-  put(0, orslot, prep(stage0, oslot, own_out, ocol, plane_of(z0 - 1)));
+#pragma unroll
+  for (int r = 0; r < RPT; ++r)
+    put(0, orslot[r], prep(stage0, oslot[r], own_out[r], ocol[r], plane_of(z0 - 1)));
   {
     wait(1);
     const float* st = stage0 + (1 % kStages) * L::STAGE;
     const int p = plane_of(z0);
-    put(1, orslot, prep(st, oslot, own_out, ocol, p));
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) put(1, orslot[r], prep(st, oslot[r], own_out[r], ocol[r], p));
     if (hslot >= 0) put_halo(1, prep(st, hslot, halo_out, hcol, p));
   }
   int sp = A.tsrc_start[tile];
   const int se = A.tsrc_start[tile + 1];
   TileSrc src{nz, 0, 0.f, 0};
   if (sp < se) src = A.tsrc[sp];
-  long long o = (long long)z0 * plane + ocol;
-  float cy = 0.f, cT = 1.f, cn = 1.f;
-  if (act) { cy = A.y[o]; cT = A.T[o]; cn = __ldg(A.nH + o); }
+  long long o = (long long)z0 * plane;   // plane offset of z (a row adds ocol[r])
+  float cy[RPT], cT[RPT], cn[RPT];
+#pragma unroll
+  for (int r = 0; r < RPT; ++r) {
+    cy[r] = 0.f; cT[r] = 1.f; cn[r] = 1.f;
+    if (act[r]) { cy[r] = A.y[o + ocol[r]]; cT[r] = A.T[o + ocol[r]]; cn[r] = __ldg(A.nH + o + ocol[r]); }
+  }
   int rkm = 0, rk = 1, rkn = 2;         // ring planes of z-1, z and z+1 (plane index mod 3)
   // stages of z and z+1 (plane index mod kStages) and the phase parity of the latter
   int skn = 2 % kStages;
@@ -247,18 +268,28 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
 
   for (int z = z0; z < z1; ++z, o += plane) {
     const int k = z - z0 + 1;           // plane index of z
-    float4 up, pp;
+    float4 up[RPT], pp[RPT];
     {
       if (!failed && !mbar_wait(&full[skn], pkn)) failed = true;
       const float* st = stage0 + skn * L::STAGE;
       const int p = plane_of(z + 1);
-      up = prep(st, oslot, own_out, ocol, p);
-      pp = put(rkn, orslot, up);
+#pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        up[r] = prep(st, oslot[r], own_out[r], ocol[r], p);
+        pp[r] = put(rkn, orslot[r], up[r]);
+      }
       if (hslot >= 0) put_halo(rkn, prep(st, hslot, halo_out, hcol, p));
     }
-    // chemistry fields of the own cell, one plane ahead
-    float ny_ = 0.f, nT_ = 1.f, nn_ = 1.f;
-    if (act && z + 1 < z1) { ny_ = A.y[o + plane]; nT_ = A.T[o + plane]; nn_ = __ldg(A.nH + o + plane); }
+    // chemistry fields of the own cells, one plane ahead
+    float ny_[RPT], nT_[RPT], nn_[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      ny_[r] = 0.f; nT_[r] = 1.f; nn_[r] = 1.f;
+      if (act[r] && z + 1 < z1) {
+        const long long on = o + plane + ocol[r];
+        ny_[r] = A.y[on]; nT_[r] = A.T[on]; nn_[r] = __ldg(A.nH + on);
+      }
+    }
     __syncthreads();
     // every thread has turned plane k+1 into ring records (before this barrier), so the stages
     // of planes up to k+1 are free: keep planes k+2 .. k+1+kStages in flight
@@ -266,42 +297,52 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       while (issued < nplanes && issued <= k + 1 + kStages) issue(issued++);
     }
-    if (act) {
-      const int c0 = rk * L::PLR + orslot, cm = rkm * L::PLR + orslot;
+    float4 u[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      if (!act[r]) continue;
+      const int c0 = rk * L::PLR + orslot[r], cm = rkm * L::PLR + orslot[r];
       const float4 uc = RU[c0], um = RU[cm];
-      float4 u;
       if (HLL) {
-        const int cp = rkn * L::PLR + orslot;
-        u = hll_update(RU + c0, RW + c0, SX + c0, SY + c0, SZ + c0, uc, um, RW[cm], SZ[cm], up,
-                       RW[cp], SZ[cp], lam);
+        const int cp = rkn * L::PLR + orslot[r];
+        u[r] = hll_update(RU + c0, RW + c0, SX + c0, SY + c0, SZ + c0, uc, um, RW[cm], SZ[cm],
+                          up[r], RW[cp], SZ[cp], lam);
       } else {
         const float4 pm = z_flux_q(um, RW[cm]);
-        u = lf_update(RU + c0, RW + c0, uc, um, pm, up, pp, cu, hl);
+        u[r] = lf_update(RU + c0, RW + c0, uc, um, pm, up[r], pp[r], cu, hl);
       }
       if (!PER) {
         float e = 0.f;
         if (gx == 0) e -= uc.y;
         if (gx == nx - 1) e += uc.y;
-        if (gy == 0) e -= uc.z;
-        if (gy == ny - 1) e += uc.z;
+        if (gy[r] == 0) e -= uc.z;
+        if (gy[r] == ny - 1) e += uc.z;
         if (z == 0) e -= uc.w;
         if (z == nz - 1) e += uc.w;
         if (e != 0.f) tl.escaped.add(lam * e);
       }
-      clamp_state(u.x, u.y, u.z, u.w, tl.clipped);
-      while (src.z == z) {
-        if (src.cell == tid) u.x += src.dN;
-        src.z = nz;
-        if (++sp < se) src = A.tsrc[sp];
-      }
-      if (SUR)
-        chem_tally_store<STD>(P, tl, cn, u, cy, cT, A.out, A.y, A.T, o, false, 0.f, 0.f, 0.f,
-                              SurDefer{P, A.sur, A.sur.buf + (size_t)tile * kSurCap,
-                                       A.sur.cnt + tile, (int)o});
-      else
-        chem_tally_store<STD>(P, tl, cn, u, cy, cT, A.out, A.y, A.T, o);
+      clamp_state(u[r].x, u[r].y, u[r].z, u[r].w, tl.clipped);
     }
-    cy = ny_; cT = nT_; cn = nn_;
+    while (src.z == z) {
+#pragma unroll
+      for (int r = 0; r < RPT; ++r)
+        if (src.cell == ocell[r]) u[r].x += src.dN;
+      src.z = nz;
+      if (++sp < se) src = A.tsrc[sp];
+    }
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      if (!act[r]) continue;
+      const long long oc = o + ocol[r];
+      if (SUR)
+        chem_tally_store<STD>(P, tl, cn[r], u[r], cy[r], cT[r], A.out, A.y, A.T, oc, false, 0.f,
+                              0.f, 0.f,
+                              SurDefer{P, A.sur, A.sur.buf + (size_t)tile * kSurCap,
+                                       A.sur.cnt + tile, (int)oc});
+      else
+        chem_tally_store<STD>(P, tl, cn[r], u[r], cy[r], cT[r], A.out, A.y, A.T, oc);
+      cy[r] = ny_[r]; cT[r] = nT_[r]; cn[r] = nn_[r];
+    }
     rkm = rk;
     rk = rkn;
     rkn = rkn == 2 ? 0 : rkn + 1;
@@ -318,70 +359,81 @@ __global__ void __launch_bounds__(kTileX * TY) k_fused_tma(const FusedArgs A,
     sur_tail<STD>(P, A.sur, A.sur.buf + (size_t)tile * kSurCap, A.sur.cnt + tile, tl, A.out,
                   A.y, A.T, RU);
   }
-  flush_tally<TY>(tl, A.slots, tile);
+  flush_tally<TYT>(tl, A.slots, tile);
 }
 
 namespace {
 
-template <int TY, bool PER>
-cudaError_t set_tma_attr() {
-  cudaError_t e = cudaFuncSetAttribute(k_fused_tma<TY, PER, false, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)Layout<TY>::BYTES);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_fused_tma<TY, PER, true, false>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Layout<TY>::BYTES);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_fused_tma<TY, PER, true, true>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Layout<TY>::BYTES);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_fused_tma<TY, PER, false, false, false, true>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Layout<TY>::BYTES);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_fused_tma<TY, PER, true, false, false, true>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Layout<TY>::BYTES);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_fused_tma<TY, PER, true, true, false, true>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Layout<TY>::BYTES);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_fused_tma<TY, PER, true, false, true>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)Layout<TY, true>::BYTES);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_fused_tma<TY, PER, true, true, true>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)Layout<TY, true>::BYTES);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_fused_tma<TY, PER, false, false, true>,
+template <int TY, bool PER, bool STD, bool FULL, bool HLL, bool SUR, int RPT>
+cudaError_t set_smem() {
+  return cudaFuncSetAttribute(k_fused_tma<TY, PER, STD, FULL, HLL, SUR, RPT>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)Layout<TY, true>::BYTES);
+                              (int)Layout<TY, HLL>::BYTES);
 }
 
 template <int TY, bool PER>
+cudaError_t set_tma_attr() {
+  const cudaError_t es[] = {
+      set_smem<TY, PER, false, false, false, false, 1>(),
+      set_smem<TY, PER, true, false, false, false, 1>(),
+      set_smem<TY, PER, true, true, false, false, 1>(),
+      set_smem<TY, PER, false, false, false, true, 1>(),
+      set_smem<TY, PER, true, false, false, true, 1>(),
+      set_smem<TY, PER, true, true, false, true, 1>(),
+      set_smem<TY, PER, false, false, true, false, 1>(),
+      set_smem<TY, PER, true, false, true, false, 1>(),
+      set_smem<TY, PER, true, true, true, false, 1>(),
+  };
+  for (cudaError_t e : es)
+    if (e != cudaSuccess) return e;
+  if constexpr (TY >= 8) {   // two rows per thread (GLF, with and without the surrogate)
+    const cudaError_t e2[] = {
+        set_smem<TY, PER, false, false, false, false, 2>(),
+        set_smem<TY, PER, true, false, false, false, 2>(),
+        set_smem<TY, PER, true, true, false, false, 2>(),
+        set_smem<TY, PER, false, false, false, true, 2>(),
+        set_smem<TY, PER, true, false, false, true, 2>(),
+        set_smem<TY, PER, true, true, false, true, 2>(),
+    };
+    for (cudaError_t e : e2)
+      if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <int TY, bool PER, int RPT>
 cudaError_t launch_tma_t(const FusedArgs& a, const TmaMaps& m, cudaStream_t s) {
   dim3 grid((a.P.nx + kTileX - 1) / kTileX, (a.P.ny + TY - 1) / TY, (a.P.nz + a.tz - 1) / a.tz);
-  dim3 block(kTileX, TY);
+  dim3 block(kTileX, TY / RPT);
   const bool full = a.P.nx % kTileX == 0 && a.P.ny % TY == 0;
-  if (a.P.hll) {   // (the standard-chemistry and full-tile instances as for GLF)
-    if (!standard_chemistry(a.P))
-      k_fused_tma<TY, PER, false, false, true><<<grid, block, Layout<TY, true>::BYTES, s>>>(a, m);
+  const bool std_ = standard_chemistry(a.P);
+  if (RPT == 1 && a.P.hll) {   // (the standard-chemistry and full-tile instances as for GLF)
+    constexpr size_t B = Layout<TY, true>::BYTES;
+    if (!std_)
+      k_fused_tma<TY, PER, false, false, true><<<grid, block, B, s>>>(a, m);
     else if (full)
-      k_fused_tma<TY, PER, true, true, true><<<grid, block, Layout<TY, true>::BYTES, s>>>(a, m);
+      k_fused_tma<TY, PER, true, true, true><<<grid, block, B, s>>>(a, m);
     else
-      k_fused_tma<TY, PER, true, false, true><<<grid, block, Layout<TY, true>::BYTES, s>>>(a, m);
+      k_fused_tma<TY, PER, true, false, true><<<grid, block, B, s>>>(a, m);
   } else if (a.sur.img) {   // the surrogate instances
-    if (!standard_chemistry(a.P))
-      k_fused_tma<TY, PER, false, false, false, true><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);
+    constexpr size_t B = Layout<TY>::BYTES;
+    if (!std_)
+      k_fused_tma<TY, PER, false, false, false, true, RPT><<<grid, block, B, s>>>(a, m);
     else if (full)
-      k_fused_tma<TY, PER, true, true, false, true><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);
+      k_fused_tma<TY, PER, true, true, false, true, RPT><<<grid, block, B, s>>>(a, m);
     else
-      k_fused_tma<TY, PER, true, false, false, true><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);
-  } else if (!standard_chemistry(a.P))
-    k_fused_tma<TY, PER, false, false><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);
-  else if (full)
-    k_fused_tma<TY, PER, true, true><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);
-  else
-    k_fused_tma<TY, PER, true, false><<<grid, block, Layout<TY>::BYTES, s>>>(a, m);
+      k_fused_tma<TY, PER, true, false, false, true, RPT><<<grid, block, B, s>>>(a, m);
+  } else if (a.P.hll) {
+    return cudaErrorInvalidConfiguration;   // (no such instance: the caller picks RPT = 1)
+  } else {
+    constexpr size_t B = Layout<TY>::BYTES;
+    if (!std_)
+      k_fused_tma<TY, PER, false, false, false, false, RPT><<<grid, block, B, s>>>(a, m);
+    else if (full)
+      k_fused_tma<TY, PER, true, true, false, false, RPT><<<grid, block, B, s>>>(a, m);
+    else
+      k_fused_tma<TY, PER, true, false, false, false, RPT><<<grid, block, B, s>>>(a, m);
+  }
   return cudaGetLastError();
 }
 
@@ -397,12 +449,21 @@ cudaError_t init_tma_attributes() {
   return set_tma_attr<16, false>();
 }
 
-cudaError_t launch_fused_tma(int ty, const FusedArgs& a, const TmaMaps& m, cudaStream_t s) {
+cudaError_t launch_fused_tma(int ty, int rpt, const FusedArgs& a, const TmaMaps& m,
+                             cudaStream_t s) {
   const bool per = a.P.bc == 0;
+  if (rpt == 2) {
+    switch (ty) {
+      case 8: return per ? launch_tma_t<8, true, 2>(a, m, s) : launch_tma_t<8, false, 2>(a, m, s);
+      case 16: return per ? launch_tma_t<16, true, 2>(a, m, s) : launch_tma_t<16, false, 2>(a, m, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (rpt != 1) return cudaErrorInvalidValue;
   switch (ty) {
-    case 4: return per ? launch_tma_t<4, true>(a, m, s) : launch_tma_t<4, false>(a, m, s);
-    case 8: return per ? launch_tma_t<8, true>(a, m, s) : launch_tma_t<8, false>(a, m, s);
-    case 16: return per ? launch_tma_t<16, true>(a, m, s) : launch_tma_t<16, false>(a, m, s);
+    case 4: return per ? launch_tma_t<4, true, 1>(a, m, s) : launch_tma_t<4, false, 1>(a, m, s);
+    case 8: return per ? launch_tma_t<8, true, 1>(a, m, s) : launch_tma_t<8, false, 1>(a, m, s);
+    case 16: return per ? launch_tma_t<16, true, 1>(a, m, s) : launch_tma_t<16, false, 1>(a, m, s);
     default: return cudaErrorInvalidValue;
   }
 }

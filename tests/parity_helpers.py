@@ -32,12 +32,15 @@ def run_oracle(state, idx, rate, run, nsteps, omp=True, **kw):
     return out, b, s
 
 
-def run_gpu(state, idx, rate, run, nsteps, mode=A.MODE_FUSED, graph_batch=100, tile=None, **kw):
+def run_gpu(state, idx, rate, run, nsteps, mode=A.MODE_FUSED, graph_batch=100, tile=None,
+            rows=None, **kw):
     a = A.from_workload(state, idx, rate, run, **kw)
     try:
         a.set_exec(mode, graph_batch)
         if tile is not None:
             a.set_tile(*tile)
+        if rows is not None:
+            a.set_tile_rows(rows)
         a.step(nsteps)
         rc = a.synchronize()
         f = a.get_fields()

@@ -123,6 +123,31 @@ def test_tiles_and_graphs_give_identical_fields(small):
             assert np.abs(a - r).max() <= 1e-5 * np.abs(r).max(), (ty, k)
 
 
+@pytest.mark.parametrize("shape,tile", [((20, 24, 36), (8, 64)), ((24, 16, 64), (8, 7)),
+                                        ((19, 22, 68), (8, 5)), ((40, 48, 32), (16, 16)),
+                                        ((11, 9, 12), (16, 4))])
+def test_two_rows_per_thread_match_one_row_and_the_oracle(shape, tile):
+    """Two rows of the tile per thread (half the warps per CTA) do the same per-cell arithmetic
+    as one row per thread, in a separately compiled kernel: within 1e-5 of it and within the
+    oracle's gates, on full tiles, x- and y-ragged tiles and both boundaries, with the one-launch
+    fused step running. Shapes are (nz, ny, nx) with nx a multiple of 4 (the TMA-staged kernel)."""
+    st, idx, rate, run = W.workload_small(shape=shape, nsrc=5, seed_field=41, seed_src=42)
+    for bc in ("periodic", "transmissive"):
+        r = dict(run, bc=bc)
+        orc, _, _ = run_oracle(st, idx, rate, r, 30)
+        f1, b1, d1, rc1 = run_gpu(st, idx, rate, r, 30, tile=tile, rows=1)
+        f2, b2, d2, rc2 = run_gpu(st, idx, rate, r, 30, tile=tile, rows=2)
+        assert rc1 == 0 and rc2 == 0
+        assert_gates(errors(f2, orc), (shape, tile, bc))
+        assert abs(budget_closure(b2)) <= 1e-6
+        for k in ("N", "Fx", "Fy", "Fz", "y", "T"):
+            scale = np.abs(f1[k]).max()
+            assert np.abs(f1[k] - f2[k]).max() <= 1e-5 * scale, (bc, k)
+        assert b2["absorbed"] == pytest.approx(b1["absorbed"], rel=1e-5)
+        assert b2["escaped"] == pytest.approx(b1["escaped"], rel=1e-5, abs=1e-9 * b1["emitted"])
+        assert d2["substeps_total"] == pytest.approx(d1["substeps_total"], rel=1e-4)
+
+
 def test_deterministic(small):
     st, idx, rate, run = small
     f1, b1, d1, _ = run_gpu(st, idx, rate, run, 20)
