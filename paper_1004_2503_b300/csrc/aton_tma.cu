@@ -386,7 +386,7 @@ cudaError_t set_tma_attr() {
   };
   for (cudaError_t e : es)
     if (e != cudaSuccess) return e;
-  if constexpr (TY >= 8) {   // two rows per thread (GLF, with and without the surrogate)
+  if constexpr (TY >= 8) {   // two rows per thread (GLF; with HLL one row measured faster)
     const cudaError_t e2[] = {
         set_smem<TY, PER, false, false, false, false, 2>(),
         set_smem<TY, PER, true, false, false, false, 2>(),
@@ -407,7 +407,10 @@ cudaError_t launch_tma_t(const FusedArgs& a, const TmaMaps& m, cudaStream_t s) {
   dim3 block(kTileX, TY / RPT);
   const bool full = a.P.nx % kTileX == 0 && a.P.ny % TY == 0;
   const bool std_ = standard_chemistry(a.P);
-  if (RPT == 1 && a.P.hll) {   // (the standard-chemistry and full-tile instances as for GLF)
+  if (a.P.hll) {   // (the standard-chemistry and full-tile instances as for GLF; one row per
+                   // thread: the HLL ring of 48 bytes per slot leaves three CTAs per SM at
+                   // tile height 8, too few warps for two rows each)
+    if (RPT != 1) return cudaErrorInvalidConfiguration;
     constexpr size_t B = Layout<TY, true>::BYTES;
     if (!std_)
       k_fused_tma<TY, PER, false, false, true><<<grid, block, B, s>>>(a, m);
@@ -423,8 +426,6 @@ cudaError_t launch_tma_t(const FusedArgs& a, const TmaMaps& m, cudaStream_t s) {
       k_fused_tma<TY, PER, true, true, false, true, RPT><<<grid, block, B, s>>>(a, m);
     else
       k_fused_tma<TY, PER, true, false, false, true, RPT><<<grid, block, B, s>>>(a, m);
-  } else if (a.P.hll) {
-    return cudaErrorInvalidConfiguration;   // (no such instance: the caller picks RPT = 1)
   } else {
     constexpr size_t B = Layout<TY>::BYTES;
     if (!std_)
