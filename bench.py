@@ -333,7 +333,7 @@ def ours(args, world, rank, local):
         a.set_exec({"tma": A.MODE_FUSED, "ldg": A.MODE_FUSED_LDG}.get(args.kernel, A.MODE_FUSED),
                    args.graph_batch)
     else:
-        ty, tz, tune_ms = a.autotune(3)
+        ty, tz, tune_ms = a.autotune(5)
     fused_mode = a.get_exec()["mode"]
     args.tile_rows = a.get_tile_rows()
     kernel = "k_fused_tma" if fused_mode == A.MODE_FUSED else "k_fused"
@@ -402,7 +402,9 @@ def ours(args, world, rank, local):
     value = replica_value(world, ncell, args.steps, t)
     ms = 1e3 * t / args.steps
 
-    # plain unfused three-kernel step at the same accuracy, from the same state
+    # plain unfused three-kernel step at the same accuracy, from the same state: the transport
+    # pass (the TMA-staged kernel's transport-only instance, one closure per cell), the source
+    # pass and the chemistry pass, each reading and writing its fields in HBM
     unfused = None
     ku = max(3, min(args.steps, 200))
     if args.no_unfused:
@@ -425,6 +427,8 @@ def ours(args, world, rank, local):
                    # its own roofline: transport (read N, F; write N, F: 32 B) and chemistry
                    # (read N, F, y, T, nH; write N, F, y, T: 52 B) as separate passes
                    "bytes_per_cell_update": PLAIN_BYTES_PER_CELL,
+                   "passes": "transport (k_fused_tma transport-only instance), sources, "
+                             "chemistry (k_plain_chem)",
                    "frac_of_hbm_at_84B": PLAIN_BYTES_PER_CELL * ncell * ku / tu / 1e9 / pk}
     a.close()
     if args.no_e2e:

@@ -187,8 +187,10 @@ static StepParams step_params(const aton_ctx* h) {
 }
 
 static int slots_needed(const aton_ctx* h) {
-  // the plain path with the surrogate uses two slot ranges of kPlainBlocks
-  return std::max(fused_tiles(h->nx, h->ny, h->nz, h->ty, h->tz), 2 * kPlainBlocks);
+  // the plain path with the surrogate uses two slot ranges of kPlainBlocks, its transport pass
+  // on the TMA-staged kernel one slot per 32 x 8 tile
+  return std::max({fused_tiles(h->nx, h->ny, h->nz, h->ty, h->tz),
+                   fused_tiles(h->nx, h->ny, h->nz, 8, h->tz), 2 * kPlainBlocks});
 }
 
 static void free_slots(Slots& s) {
@@ -409,6 +411,20 @@ static int enqueue_step(aton_handle h, cudaStream_t s) {
       a.sur_resid = (float)h->sur_p.residual_max;
       a.sur_list = h->sur_list;
       a.sur_count = h->sur_count;
+    }
+    // the transport pass on the TMA-staged kernel (one closure per cell) where the grid allows
+    // it and the flux is GLF; otherwise k_plain_transport
+    if (h->prm.flux == ATON_FLUX_GLF && h->tma_ok[ty_index(8)]) {
+      FusedArgs t{};
+      t.P = a.P;
+      t.in = in; t.out = out;
+      t.y = h->y; t.T = h->T; t.nH = h->nH;
+      t.slots = h->slots;
+      t.tz = h->tz;
+      t.in_buf = h->cur;
+      e = launch_transport_tma(t, h->tma[ty_index(8)], s);
+      if (e != cudaSuccess) return fail(ATON_ERR_CUDA, "transport launch: %s", cudaGetErrorString(e));
+      a.transported = true;
     }
     e = launch_plain_step(a, s);
     if (h->sink) h->sink_steps += 1;

@@ -103,6 +103,8 @@ struct PlainArgs {
   float sur_gate, sur_resid;
   int* sur_list;        // candidate cells of the step (capacity ncell)
   int* sur_count;       // number of candidates (reset before every chemistry pass)
+  bool transported;     // the transport pass already ran (launch_transport_tma): sources and
+                        // chemistry only
 };
 
 // The standard chemistry configuration (evolving temperature, cooling and collisional
@@ -129,6 +131,8 @@ cudaError_t init_kernel_attributes();
 cudaError_t init_tma_attributes();
 cudaError_t launch_fused_tma(int ty, int rpt, const FusedArgs& a, const TmaMaps& m,
                              cudaStream_t s);
+// the transport pass of the plain step on the TMA-staged kernel (tile 32 x 8; GLF flux)
+cudaError_t launch_transport_tma(const FusedArgs& a, const TmaMaps& m8, cudaStream_t s);
 bool make_tma_maps(int nx, int ny, int nz, int ty, float* const u[2][4], TmaMaps* out);
 cudaError_t launch_fused(int ty, const FusedArgs& a, cudaStream_t s);
 int fused_tiles(int nx, int ny, int nz, int ty, int tz);

@@ -447,7 +447,8 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain_chem_sur(const PlainArg
 int plain_launches() { return 3; }
 
 cudaError_t launch_plain_step(const PlainArgs& a, cudaStream_t s) {
-  if (a.P.hll) {
+  if (a.transported) {
+  } else if (a.P.hll) {
     if (a.P.bc == 0) k_plain_transport<true, true><<<kPlainBlocks, kPlainThreads, 0, s>>>(a);
     else k_plain_transport<false, true><<<kPlainBlocks, kPlainThreads, 0, s>>>(a);
   } else {

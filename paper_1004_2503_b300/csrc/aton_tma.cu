@@ -111,13 +111,20 @@ struct Layout {
 // the accepted predictions replacing the exact operator. RPT: rows of the tile per thread (the
 // CTA has TY / RPT warps; thread row t owns the rows t RPT .. t RPT + RPT - 1), which spreads
 // the per-plane work that does not depend on the cell count (the stage wait, the barrier, the
-// loop) and the halo rows over more cells.
-template <int TY, bool PER, bool STD, bool FULL, bool HLL = false, bool SUR = false, int RPT = 1>
-__global__ void __launch_bounds__(kTileX * TY / RPT) k_fused_tma(const FusedArgs A,
+// loop) and the halo rows over more cells. TO: transport only (the first kernel of the plain
+// three-kernel step): the transported and clamped (N, F) are stored, without sources or
+// chemistry, and y, T, nH are not read.
+template <int TY, bool PER, bool STD, bool FULL, bool HLL = false, bool SUR = false, int RPT = 1,
+          bool TO = false>
+// (the surrogate instance at tile 32 x 8 with two rows is held to five CTAs per SM, like the
+// exact one: its network tail after the z-loop would otherwise raise the register count)
+__global__ void __launch_bounds__(kTileX * TY / RPT, (SUR && RPT == 2 && TY == 8) ? 5 : 1)
+    k_fused_tma(const FusedArgs A,
                                                                  const __grid_constant__ TmaMaps M) {
   using L = Layout<TY, HLL>;
   constexpr int TX = kTileX, NH = 2 * TX + 2 * TY, TYT = TY / RPT;
   static_assert(TY % RPT == 0 && TX * TYT >= NH, "one halo slot per thread at most");
+  static_assert(!(TO && SUR), "transport only: no chemistry");
   extern __shared__ __align__(128) float sm_raw[];
   // 128-byte aligned base for the TMA boxes, as an offset from the shared array (so every
   // access below stays a shared-memory access)
@@ -250,8 +257,8 @@ __global__ void __launch_bounds__(kTileX * TY / RPT) k_fused_tma(const FusedArgs
     for (int r = 0; r < RPT; ++r) put(1, orslot[r], prep(st, oslot[r], own_out[r], ocol[r], p));
     if (hslot >= 0) put_halo(1, prep(st, hslot, halo_out, hcol, p));
   }
-  int sp = A.tsrc_start[tile];
-  const int se = A.tsrc_start[tile + 1];
+  int sp = TO ? 0 : A.tsrc_start[tile];   // (the transport-only pass has no source lists)
+  const int se = TO ? 0 : A.tsrc_start[tile + 1];
   TileSrc src{nz, 0, 0.f, 0};
   if (sp < se) src = A.tsrc[sp];
   long long o = (long long)z0 * plane;   // plane offset of z (a row adds ocol[r])
@@ -259,7 +266,7 @@ __global__ void __launch_bounds__(kTileX * TY / RPT) k_fused_tma(const FusedArgs
 #pragma unroll
   for (int r = 0; r < RPT; ++r) {
     cy[r] = 0.f; cT[r] = 1.f; cn[r] = 1.f;
-    if (act[r]) { cy[r] = A.y[o + ocol[r]]; cT[r] = A.T[o + ocol[r]]; cn[r] = __ldg(A.nH + o + ocol[r]); }
+    if (!TO && act[r]) { cy[r] = A.y[o + ocol[r]]; cT[r] = A.T[o + ocol[r]]; cn[r] = __ldg(A.nH + o + ocol[r]); }
   }
   int rkm = 0, rk = 1, rkn = 2;         // ring planes of z-1, z and z+1 (plane index mod 3)
   // stages of z and z+1 (plane index mod kStages) and the phase parity of the latter
@@ -285,7 +292,7 @@ __global__ void __launch_bounds__(kTileX * TY / RPT) k_fused_tma(const FusedArgs
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
       ny_[r] = 0.f; nT_[r] = 1.f; nn_[r] = 1.f;
-      if (act[r] && z + 1 < z1) {
+      if (!TO && act[r] && z + 1 < z1) {
         const long long on = o + plane + ocol[r];
         ny_[r] = A.y[on]; nT_[r] = A.T[on]; nn_[r] = __ldg(A.nH + on);
       }
@@ -323,7 +330,7 @@ __global__ void __launch_bounds__(kTileX * TY / RPT) k_fused_tma(const FusedArgs
       }
       clamp_state(u[r].x, u[r].y, u[r].z, u[r].w, tl.clipped);
     }
-    while (src.z == z) {
+    while (!TO && src.z == z) {
 #pragma unroll
       for (int r = 0; r < RPT; ++r)
         if (src.cell == ocell[r]) u[r].x += src.dN;
@@ -334,7 +341,10 @@ __global__ void __launch_bounds__(kTileX * TY / RPT) k_fused_tma(const FusedArgs
     for (int r = 0; r < RPT; ++r) {
       if (!act[r]) continue;
       const long long oc = o + ocol[r];
-      if (SUR)
+      if (TO) {   // the transported state, physical F
+        A.out.N[oc] = u[r].x;
+        A.out.Fx[oc] = u[r].y * P.c; A.out.Fy[oc] = u[r].z * P.c; A.out.Fz[oc] = u[r].w * P.c;
+      } else if (SUR)
         chem_tally_store<STD>(P, tl, cn[r], u[r], cy[r], cT[r], A.out, A.y, A.T, oc, false, 0.f,
                               0.f, 0.f,
                               SurDefer{P, A.sur, A.sur.buf + (size_t)tile * kSurCap,
@@ -467,6 +477,33 @@ cudaError_t launch_fused_tma(int ty, int rpt, const FusedArgs& a, const TmaMaps&
     case 16: return per ? launch_tma_t<16, true, 1>(a, m, s) : launch_tma_t<16, false, 1>(a, m, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// The transport-only instance (tile 32 x 8, two rows per thread, GLF flux) of the plain
+// three-kernel step: the plain step's transport pass, with one closure evaluation per cell.
+namespace {
+template <bool PER, bool FULL>
+cudaError_t launch_to(const FusedArgs& a, const TmaMaps& m, cudaStream_t s) {
+  using K = Layout<8>;
+  static bool attr = false;   // (set once per process, before the first launch)
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute(
+        k_fused_tma<8, PER, false, FULL, false, false, 2, true>,
+        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((a.P.nx + kTileX - 1) / kTileX, (a.P.ny + 7) / 8, (a.P.nz + a.tz - 1) / a.tz);
+  k_fused_tma<8, PER, false, FULL, false, false, 2, true><<<grid, dim3(kTileX, 4), K::BYTES, s>>>(a, m);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_transport_tma(const FusedArgs& a, const TmaMaps& m8, cudaStream_t s) {
+  if (a.P.hll) return cudaErrorInvalidConfiguration;
+  const bool full = a.P.nx % kTileX == 0 && a.P.ny % 8 == 0;
+  if (a.P.bc == 0) return full ? launch_to<true, true>(a, m8, s) : launch_to<true, false>(a, m8, s);
+  return full ? launch_to<false, true>(a, m8, s) : launch_to<false, false>(a, m8, s);
 }
 
 // Tensor maps of the radiation fields for a tile height ty: for each ping-pong buffer and each

@@ -47,16 +47,19 @@ def test_lognormal_periodic_100_steps(small, small_oracle, mode):
 
 @pytest.mark.parametrize("fixed_T", [0, 1])
 def test_stromgren_32_transmissive(fixed_T):
+    """Transmissive 32^3 box with one source, through the fused step and the plain three-kernel
+    step (whose transport pass is the TMA-staged kernel's transport-only instance here)."""
     st, idx, rate, run = W.workload_32()
     kw = dict(fixed_T=fixed_T, coll_ion=0 if fixed_T else 1)
     orc, ob, _ = run_oracle(st, idx, rate, run, 100, **kw)
-    f, b, d, rc = run_gpu(st, idx, rate, run, 100, **kw)
-    assert rc == 0
-    e = errors(f, orc)
-    print("errors", kw, e)
-    assert_gates(e)
-    assert abs(budget_closure(b)) <= 1e-6
-    assert b["escaped"] == pytest.approx(ob["escaped"], rel=1e-3, abs=1e-6 * ob["emitted"])
+    for mode in (A.MODE_FUSED, A.MODE_UNFUSED):
+        f, b, d, rc = run_gpu(st, idx, rate, run, 100, mode=mode, **kw)
+        assert rc == 0
+        e = errors(f, orc)
+        print("errors", kw, mode, e)
+        assert_gates(e, mode)
+        assert abs(budget_closure(b)) <= 1e-6
+        assert b["escaped"] == pytest.approx(ob["escaped"], rel=1e-3, abs=1e-6 * ob["emitted"])
 
 
 @pytest.mark.parametrize("shape,tile", [((40, 1, 1), (4, 7)), ((2, 3, 5), (8, 1)),
