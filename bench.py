@@ -266,10 +266,62 @@ def surrogate_leg(args):
             "ionised_atoms_rel_err": ion(su["x"]) / ion(ex["x"]) - 1,
             "max_abs_dx": float(np.abs(su["x"] - ex["x"]).max()),
             "budget_closure": su["clos"]}
+    res["front_cells_128"] = front_cells_leg(m, args)
     m.close()
     return {"path": "fused step, network in the same launch", "residual_max": 1e-4, "gate_substeps": 8.0,
             "train_records": int(rec.shape[0]), "pair_collection_seconds": t1 - t0,
             "train_seconds": t2 - t1, "train_steps": 3000, "batch": 16384, **res}
+
+
+def front_cells_leg(m, args):
+    """Where the exact operator sub-cycles heavily: a periodic 128^3 box whose every cell is
+    drawn from the pair records of the exact operator that took >= 4 sub-steps, on lognormal
+    boxes of the training recipe with seeds 300-303 (disjoint from training and evaluation);
+    F = 0, no sources. One step from that state (best of three, no graphs), exact and with the
+    surrogate at residual thresholds 1e-4 and 1e-3, in the plain three-kernel mode for both (its
+    chemistry pass lists every candidate device-wide; the fused kernel lists at most 64 per
+    CTA)."""
+    import torch
+    from paper_1004_2503_b300 import aton as A
+    from paper_1004_2503_b300 import surrogate as S
+    wl = list(S.training_boxes(range(300, 304), n=64, sigma_ln=1.5, nsrc=8))
+    rec = S.collect_pairs(wl, steps=120, stride=1, capacity=20_000_000, keep_light=0.0)
+    st, idx, rate, run = S.front_cells_box(rec, 128, wl[0][3], min_substeps=4)
+    ncell = st["N"].size
+    out = {"cells": ncell, "records_ge4_substeps": int((rec[:, 7] >= 4).sum()),
+           "records_gt1_substep": int(rec.shape[0])}
+    ex = None
+    for name, resid in (("exact", None), ("surrogate_1e-4", 1e-4), ("surrogate_1e-3", 1e-3)):
+        best = None
+        for _ in range(3):
+            a = A.from_workload(st, idx, rate, run)
+            s = torch.cuda.Stream()
+            a.set_stream(s)
+            a.set_exec(A.MODE_UNFUSED, 0)
+            if resid is not None:
+                a.set_surrogate(m, gate_substeps=8.0, residual_max=resid)
+            a.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            a.step(1)
+            e1.record(s)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            if best is None or ms < best[0]:
+                f, b, d = a.get_fields(), a.photon_budget(), a.diag()
+                best = (ms, float(np.sum(st["nH"].astype(np.float64) * f["x"])), b["absorbed"], d)
+            a.close()
+        ms, ion, ab, d = best
+        r = {"ms": ms, "substeps_per_cell": d["substeps_total"] / ncell,
+             "network_fraction": d["surrogate_cells"] / ncell}
+        if ex is None:
+            ex = best
+        else:
+            r.update(speedup=ex[0] / ms, ionised_atoms_rel_err=ion / ex[1] - 1,
+                     absorbed_rel_err=ab / ex[2] - 1)
+        out[name] = r
+    return out
 
 
 def reference_arm(args, world, rank):

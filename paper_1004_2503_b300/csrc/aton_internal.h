@@ -18,7 +18,7 @@ namespace aton {
 constexpr int kTileX = 32;          // cells per CTA row in x (one warp)
 constexpr int kPlainBlocks = 148 * 8;  // fixed grid of the unfused kernels (deterministic slots)
 constexpr int kPlainThreads = 256;
-constexpr int kSurBlocks = 148;        // grid of the surrogate pass (few candidate cells)
+constexpr int kSurBlocks = kPlainBlocks;  // grid of the surrogate pass (CTAs without candidates exit)
 
 // One point source of a fused tile: plane z, cell (tx + 32*ty) inside the tile, dN added.
 struct TileSrc {

@@ -95,3 +95,20 @@ def train_on_lognormal_boxes(seeds=range(100, 112), n=64, sigma_ln=1.5, nsrc=8, 
     dt = wl[0][3]["dt"]
     train(m, rec, dt, steps=train_steps, batch=batch)
     return m, int(rec.shape[0]), dt
+
+
+def front_cells_box(records, n, run, min_substeps=4, seed=7):
+    """A periodic n^3 box of front-condition cells: every cell's (nH, N, y, T) drawn (seeded,
+    with replacement) from the pair records whose exact operator took at least `min_substeps`
+    sub-steps; F = 0, no sources. Returns (state, src_idx, src_rate, run) like the workload
+    builders; `run` gives the cell size and time step of the runs the records came from."""
+    rec = records[records[:, 7] >= min_substeps].cpu().numpy()
+    if rec.shape[0] == 0:
+        raise ValueError("no record with that many sub-steps")
+    pick = rec[np.random.default_rng(seed).integers(0, rec.shape[0], n ** 3)]
+    st = {k: pick[:, j].reshape(n, n, n).astype(np.float32)
+          for k, j in (("nH", 0), ("N", 1), ("y", 2), ("T", 3))}
+    st["x"] = (1.0 - st["y"]).astype(np.float32)
+    for k in ("Fx", "Fy", "Fz"):
+        st[k] = np.zeros((n, n, n), np.float32)
+    return st, np.zeros(0, np.int64), np.zeros(0, np.float64), dict(run, nx=n, ny=n, nz=n)

@@ -169,3 +169,47 @@ def test_stromgren_256_front_within_one_cell_of_the_oracle(trained_surrogate, re
     assert bad == 0
     if residual >= 1e-3:
         assert d["surrogate_cells"] > 0
+
+
+def test_front_cells_exact_step_and_what_the_network_saves(trained_surrogate):
+    """Front-condition cells, where the exact operator sub-cycles heavily: a periodic 48^3 box
+    whose every cell is drawn from the pair records that took >= 4 sub-steps, on lognormal boxes
+    of the training recipe with seeds 300-301 (disjoint from training and evaluation); F = 0.
+    One step in the plain three-kernel mode: the exact step matches the oracle within the parity
+    gates on x and T; on N within 1e-3 relative plus 1e-6 of the box's mean incoming photon
+    density (a cell that absorbs all but ~3e-5 of its photons, optical depth ~10, keeps N' with
+    the relative error of its optical depth times ~10: measured up to 2.4e-3 relative, 6e-13
+    absolute against ~1e-5 incoming, while x and T agree to 1e-6); and with the surrogate at
+    residual 1e-3 the network takes part of the cells, which
+    saves their sub-steps, while the ionised atoms stay within 1e-3 of the oracle's and the
+    absorbed photons within 1e-2 (the residual test bounds each accepted cell's photon balance,
+    not its absorption alone)."""
+    from paper_1004_2503_b300 import surrogate as S
+    from parity_helpers import errors
+    wl = list(S.training_boxes(range(300, 302), n=64, sigma_ln=1.5, nsrc=8))
+    rec = S.collect_pairs(wl, steps=120, stride=1, capacity=10_000_000, keep_light=0.0)
+    st, idx, rate, run = S.front_cells_box(rec, 48, wl[0][3], min_substeps=4)
+    ncell = st["N"].size
+    orc, ob, _ = run_oracle(st, idx, rate, run, 1)
+    fe, be, de, _ = _run(st, idx, rate, run, 1, mode=A.MODE_UNFUSED)
+    assert de["substeps_total"] >= 4 * ncell          # heavy: several sub-steps per cell
+    e = errors(fe, orc)
+    print("front cells, exact: errors", e)
+    assert e["x_abs"] <= 1e-3 and e["T_rel"] <= 1e-3, e
+    dN = np.abs(fe["N"].astype(np.float64) - orc["N"])
+    assert np.all(dN <= 1e-3 * orc["N"] + 1e-6 * float(np.mean(st["N"]))), float(dN.max())
+    def closure(b):   # (no sources: relative to the photons the box starts with)
+        return (b["stored0"] - b["stored"] - b["absorbed"] - b["escaped"] - b["clipped"]) / b["stored0"]
+
+    assert abs(closure(be)) <= 1e-6
+    fs, bs, ds, _ = _run(st, idx, rate, run, 1, trained_surrogate, residual=1e-3,
+                         mode=A.MODE_UNFUSED)
+    ion, ion_o = float(np.sum(st["nH"] * fs["x"])), float(np.sum(st["nH"] * orc["x"]))
+    print("front cells: exact sub-steps/cell", de["substeps_total"] / ncell, "surrogate",
+          ds["substeps_total"] / ncell, "network fraction", ds["surrogate_cells"] / ncell,
+          "ionised atoms rel", ion / ion_o - 1, "absorbed rel", bs["absorbed"] / ob["absorbed"] - 1)
+    assert ds["surrogate_cells"] >= 0.02 * ncell
+    assert ds["substeps_total"] <= 0.97 * de["substeps_total"]
+    assert ion == pytest.approx(ion_o, rel=1e-3)
+    assert bs["absorbed"] == pytest.approx(ob["absorbed"], rel=1e-2)
+    assert abs(closure(bs)) <= 1e-6
