@@ -171,7 +171,7 @@ int aton_get_tile_rows(aton_handle h, int* rows);
  * copy of the current state for each candidate tile (and, for the TMA-staged kernel, one or two
  * rows per thread) and keeps the fastest kernel and tile (the
  * simulation state is not advanced; an unfused mode stays unfused). `steps` per candidate
- * (>= 1). Writes the chosen (ty, tz) and its time per step [ms] when the pointers are not NULL;
+ * (>= 1), then the three fastest once more over 3 x `steps` (short timings are noisy). Writes the chosen (ty, tz) and its time per step [ms] when the pointers are not NULL;
  * aton_get_exec reports the chosen mode. */
 int aton_autotune(aton_handle h, int steps, int* ty_out, int* tz_out, float* ms_out);
 
