@@ -227,13 +227,26 @@ __device__ __forceinline__ float4 hll_axis(const float4& fl, const float4& fc, c
                      hll_face(kp, fc.w, fh.w, uc.w, uh.w) - hll_face(km, fl.w, fc.w, ul.w, uc.w));
 }
 
-// HLL update of the centre cell: u' = u - lam sum_d (F_{d,+} - F_{d,-}). U, W, SX, SY point at
-// the centre slot of plane z; the z neighbours come as (state, closure pair, z speeds).
-__device__ __forceinline__ float4 hll_update(const float4* U, const float2* W, const float2* SX,
-                                             const float2* SY, const float2* SZ, const float4& uc,
-                                             const float4& um, const float2& qm,
-                                             const float2& szm, const float4& up,
-                                             const float2& qp, const float2& szp, float lam) {
+// HLL flux through the face between a cell L and the cell R above it along z (the same numbers
+// as hll_axis's faces along z, so that the flux a plane's update computes for its upper face is
+// the one the next plane's update needs for its lower face)
+__device__ __forceinline__ float4 hll_zface(const float4& uL, const float2& qL, const float2& sL,
+                                            const float4& uR, const float2& qR, const float2& sR) {
+  const HllCoef k = hll_coef(fminf(0.f, fminf(sL.x, sR.x)), fmaxf(0.f, fmaxf(sL.y, sR.y)));
+  const float4 fL = z_flux_q(uL, qL), fR = z_flux_q(uR, qR);
+  return make_float4(hll_face(k, fL.x, fR.x, uL.x, uR.x), hll_face(k, fL.y, fR.y, uL.y, uR.y),
+                     hll_face(k, fL.z, fR.z, uL.z, uR.z), hll_face(k, fL.w, fR.w, uL.w, uR.w));
+}
+
+// HLL update of the centre cell: u' = u - lam sum_d (F_{d,+} - F_{d,-}). U, W, SX, SY, SZ point
+// at the centre slot of plane z; the z neighbour above comes as (state, closure pair, z speeds),
+// the lower z face's flux fm as carried from the previous plane's update (its upper face, which
+// this update returns in fp): one z face evaluated per cell instead of two.
+__device__ __forceinline__ float4 hll_update_zc(const float4* U, const float2* W, const float2* SX,
+                                                const float2* SY, const float2* SZ,
+                                                const float4& uc, const float4& up,
+                                                const float2& qp, const float2& szp,
+                                                const float4& fm, float4& fp, float lam) {
   constexpr int RX = kRingRX;
   const float2 qc = W[0];
   const float4 uL = U[-1], uR = U[1], uD = U[-RX], uU = U[RX];
@@ -241,8 +254,8 @@ __device__ __forceinline__ float4 hll_update(const float4* U, const float2* W, c
                              uR, SX[-1], SX[0], SX[1]);
   const float4 ay = hll_axis(y_flux_q(uD, W[-RX]), y_flux_q(uc, qc), y_flux_q(uU, W[RX]), uD,
                              uc, uU, SY[-RX], SY[0], SY[RX]);
-  const float4 az = hll_axis(z_flux_q(um, qm), z_flux_q(uc, qc), z_flux_q(up, qp), um, uc, up,
-                             szm, SZ[0], szp);
+  fp = hll_zface(uc, qc, SZ[0], up, qp, szp);
+  const float4 az = make_float4(fp.x - fm.x, fp.y - fm.y, fp.z - fm.z, fp.w - fm.w);
   return make_float4(uc.x - lam * ((ax.x + ay.x) + az.x), uc.y - lam * ((ax.y + ay.y) + az.y),
                      uc.z - lam * ((ax.z + ay.z) + az.z), uc.w - lam * ((ax.w + ay.w) + az.w));
 }

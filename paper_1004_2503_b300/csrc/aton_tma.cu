@@ -270,6 +270,16 @@ __global__ void __launch_bounds__(kTileX * TY / RPT, (SUR && RPT == 2 && TY == 8
     cy[r] = 0.f; cT[r] = 1.f; cn[r] = 1.f;
     if (!TO && act[r]) { cy[r] = A.y[o + ocol[r]]; cT[r] = A.T[o + ocol[r]]; cn[r] = __ldg(A.nH + o + ocol[r]); }
   }
+  // HLL: the flux through each own cell's lower z face, carried from plane to plane (the first
+  // from ring planes 0 and 1, planes z0-1 and z0)
+  float4 fzm[RPT];
+  if (HLL) {
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int c0 = orslot[r], c1 = L::PLR + orslot[r];
+      fzm[r] = hll_zface(RU[c0], RW[c0], SZ[c0], RU[c1], RW[c1], SZ[c1]);
+    }
+  }
   int rkm = 0, rk = 1, rkn = 2;         // ring planes of z-1, z and z+1 (plane index mod 3)
   // stages of z and z+1 (plane index mod kStages) and the phase parity of the latter
   int skn = 2 % kStages;
@@ -311,11 +321,13 @@ __global__ void __launch_bounds__(kTileX * TY / RPT, (SUR && RPT == 2 && TY == 8
     for (int r = 0; r < RPT; ++r) {
       if (!act[r]) continue;
       const int c0 = rk * L::PLR + orslot[r], cm = rkm * L::PLR + orslot[r];
-      const float4 uc = RU[c0], um = RU[cm];
+      const float4 uc = RU[c0], um = RU[cm];   // (um: GLF only)
       if (HLL) {
         const int cp = rkn * L::PLR + orslot[r];
-        u[r] = hll_update(RU + c0, RW + c0, SX + c0, SY + c0, SZ + c0, uc, um, RW[cm], SZ[cm],
-                          up[r], RW[cp], SZ[cp], lam);
+        float4 fzp;
+        u[r] = hll_update_zc(RU + c0, RW + c0, SX + c0, SY + c0, SZ + c0, uc, up[r], RW[cp],
+                             SZ[cp], fzm[r], fzp, lam);
+        fzm[r] = fzp;
       } else {
         const float4 pm = z_flux_q(um, RW[cm]);
         u[r] = lf_update(RU + c0, RW + c0, uc, um, pm, up[r], pp[r], cu, hl);
