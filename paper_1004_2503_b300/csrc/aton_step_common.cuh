@@ -306,15 +306,17 @@ __device__ __forceinline__ bool sur_accept(const StepParams& P, const MlpNorm& n
 }
 
 // The network for the cells of one warp (all 32 lanes call this together): the MLP for the
-// warp's 32 cells on tensor cores (two 16-row m16n8k16 passes of mlp_infer16_sh, weights read
-// through L1 from the device image, activations in the warp's shared-memory tiles H1, H2);
+// warp's 32 cells on tensor cores (two 16-row m16n8k16 passes of mlp_infer16_sh with the weights
+// W, a shared-memory copy in the fused kernel's tail, activations in the warp's shared-memory
+// tiles H1, H2);
 // each lane with `cand` set decodes and checks its own prediction. Returns whether this lane's prediction
 // was accepted (then N1, y1, T1 hold it). Features are exchanged with shuffles: lane (g, t) of a
 // 16-row pass needs features 2t, 2t+1 of rows g and g+8, and a row's three outputs sit in the
 // lanes 4 (row mod 8) and 4 (row mod 8) + 1.
-__device__ __forceinline__ bool sur_warp(const StepParams& P, const SurList& S, bool cand, float n,
-                                         float N, float y, float T, float& N1, float& y1,
-                                         float& T1, __nv_bfloat16* H1, __nv_bfloat16* H2) {
+__device__ __forceinline__ bool sur_warp(const StepParams& P, const SurList& S, const MlpImage& W,
+                                         bool cand, float n, float N, float y, float T, float& N1,
+                                         float& y1, float& T1, __nv_bfloat16* H1,
+                                         __nv_bfloat16* H2) {
   const unsigned full = 0xffffffffu;
   const MlpNorm& nm = *S.norm;
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
@@ -339,7 +341,7 @@ __device__ __forceinline__ bool sur_warp(const StepParams& P, const SurList& S, 
     const float b1 = t == 0 ? fb[1] : (t == 1 ? fb[3] : 0.f);
     const unsigned a[4] = {pack_bf16(a0, a1), pack_bf16(b0, b1), 0u, 0u};
     float yo[4];
-    mlp_infer16_sh(*S.img, a, H1, H2, yo);
+    mlp_infer16_sh(W, a, H1, H2, yo);
     const int r = lane - half * 16;
     const int s0 = 4 * (r & 7);
     const float c0 = __shfl_sync(full, yo[0], s0), c1 = __shfl_sync(full, yo[1], s0);
@@ -410,9 +412,14 @@ __device__ __forceinline__ void chem_tally_store(const StepParams& P, Tally& tl,
 // The end of a fused CTA with the surrogate: its listed cells, 32 per warp (warps 0 and 1),
 // run through the network; accepted predictions are stored, the others take the exact operator
 // (their latency overlaps with the other CTAs on the SM). Called by every thread of the CTA
-// after its z-loop. `scratch`: shared memory free by then (the plane ring), at least
-// 2 x 2 x 16 x kP2 BF16 (9216 bytes).
-constexpr int kSurScratchBytes = 2 * 2 * 16 * kP2 * 2;
+// after its z-loop. `scratch`: shared memory free by then (the stage and plane rings), 16-byte
+// aligned, at least sizeof(MlpImage) bytes. A CTA with listed cells first copies the forward
+// weights and biases into it with one coalesced pass (the network's weight reads would otherwise
+// be dependent round trips to L2, about 44 per 16 rows), laid out as an MlpImage whose backward
+// blocks (W2T, W3T) are not copied and hold the two warps' activation tiles instead.
+constexpr int kSurScratchBytes = (int)sizeof(MlpImage);
+static_assert(2 * 2 * 16 * kP2 * 2 <= sizeof(MlpImage::W2T) + sizeof(MlpImage::W3T),
+              "activation tiles fit in the backward blocks");
 template <bool STD>
 __device__ __forceinline__ void sur_tail(const StepParams& P, const SurList& S, const SurRec* buf,
                                          int* cnt, Tally& tl, const Fields& out, float* Yf,
@@ -421,23 +428,35 @@ __device__ __forceinline__ void sur_tail(const StepParams& P, const SurList& S, 
   __syncthreads();   // (orders the list's writes, global memory included, before its reads)
   const int nc = min(*reinterpret_cast<volatile int*>(cnt), kSurCap);
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nthr = blockDim.x * blockDim.y;
+  if (nc == 0) return;   // (uniform over the CTA)
+  MlpImage& Ws = *reinterpret_cast<MlpImage*>(scratch);
+  {
+    constexpr int kFwd = (int)(offsetof(MlpImage, W2T) / 16);            // W1, W2, W3
+    constexpr int kBias0 = (int)(offsetof(MlpImage, b1) / 16);
+    constexpr int kBias1 = (int)((sizeof(MlpImage) + 15) / 16);
+    const uint4* src = reinterpret_cast<const uint4*>(S.img);
+    uint4* dst = reinterpret_cast<uint4*>(&Ws);
+    for (int i = tid; i < kFwd; i += nthr) dst[i] = src[i];
+    for (int i = kBias0 + tid; i < kBias1; i += nthr) dst[i] = src[i];
+  }
+  __syncthreads();
   const int w = tid >> 5, lane = tid & 31;
   if (w < 2 && w * 32 < nc) {   // (uniform within the warp)
-    __nv_bfloat16* H1 = reinterpret_cast<__nv_bfloat16*>(scratch) + w * 2 * 16 * kP2;
+    __nv_bfloat16* H1 = reinterpret_cast<__nv_bfloat16*>(&Ws.W2T[0]) + w * 2 * 16 * kP2;
     __nv_bfloat16* H2 = H1 + 16 * kP2;
     const int k = w * 32 + lane;
     const bool valid = k < nc;
     const SurRec r = valid ? buf[k] : SurRec{0.f, 0.f, 0.f, 0.f, 1.f, 1e4f, 1.f, 0};
     float N1 = 0.f, y1 = 0.f, T1 = 0.f;
-    const bool acc = sur_warp(P, S, valid, r.n, r.N, r.y, r.T, N1, y1, T1, H1, H2);
+    const bool acc = sur_warp(P, S, Ws, valid, r.n, r.N, r.y, r.T, N1, y1, T1, H1, H2);
     if (valid)
       chem_tally_store<STD>(P, tl, r.n, make_float4(r.N, r.X, r.Y, r.Z), r.y, r.T, out, Yf, Tf,
                             r.o, acc, N1, y1, T1);
   }
-  if (nc > 0) {   // the next step's list starts empty (every thread has read the count)
-    __syncthreads();
-    if (tid == 0) *cnt = 0;
-  }
+  // the next step's list starts empty (every thread has read the count)
+  __syncthreads();
+  if (tid == 0) *cnt = 0;
 }
 
 }  // namespace aton

@@ -379,9 +379,10 @@ __global__ void __launch_bounds__(kTileX * TY / RPT, (SUR && RPT == 2 && TY == 8
     for (int k = max(0, issued - kStages); k < issued; ++k)
       mbar_wait(&full[k % kStages], (k / kStages) & 1);
   if (SUR) {
-    static_assert(!SUR || L::RING_BYTES >= kSurScratchBytes, "ring too small for the network");
+    static_assert(!SUR || L::STAGE_BYTES + L::RING_BYTES >= kSurScratchBytes,
+                  "stage and plane rings too small for the network");
     sur_tail<STD>(P, A.sur, A.sur.buf + (size_t)tile * kSurCap, A.sur.cnt + tile, tl, A.out,
-                  A.y, A.T, RU);
+                  A.y, A.T, sm);
   }
   flush_tally<TYT>(tl, A.slots, tile);
 }
