@@ -170,7 +170,7 @@ __device__ __forceinline__ void mlp_forward16(const MlpImage& W, const unsigned 
 // tile H (16 rows x kP2 BF16, twice: layer 1 and layer 2) instead of registers, and the output
 // tiles are not unrolled, so only one accumulator tile and one operand set are live. For the
 // fused step kernel, whose register count the rarely used network must not raise. W may sit in
-// global memory (read through L1).
+// shared memory (the fused kernel's tail copies it there) or in global memory (read through L1).
 __device__ __forceinline__ void mlp_infer16_sh(const MlpImage& W, const unsigned xa[4],
                                                __nv_bfloat16* H1, __nv_bfloat16* H2, float y[4]) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
