@@ -83,3 +83,36 @@ def test_stromgren_32_front_follows_the_closed_form():
         assert b["escaped"] < 2e-2 * b["emitted"]
     finally:
         a.close()
+
+
+def test_photoionisation_equilibrium_of_a_uniformly_lit_box():
+    """A periodic uniform box (32^3, nH = 1 cm^-3, T = 1e4 K fixed, no collisional ionisation)
+    with an identical source in every cell: the field stays uniform, and at steady state the
+    recombinations balance the emission, alpha_B nH^2 x^2 = Ndot / V (section 3.2.1, the balance
+    of Eq. 14 with the photo-ionisations equal to the photons injected), here x = 0.5. The step
+    is 1/100 of the recombination time, 3000 steps: the GPU's x within 2e-3 of 0.5 in every
+    cell, the photon budget closed."""
+    from paper_1004_2503_b300 import aton as A
+    n, T, x_eq = 1.0, 1e4, 0.5
+    lam = 2 * 157807.0 / T
+    aB = 2.753e-14 * lam ** 1.5 / (1 + (lam / 2.740) ** 0.407) ** 2.242   # case B (Hui & Gnedin)
+    m = 32
+    dt = 0.01 / (aB * n)
+    dx = 3.0 * W.C_LIGHT * dt / 0.9          # the CFL-limited step of this cell size is dt
+    shape = (m, m, m)
+    st = W.initial_state(np.full(shape, n), T, 1e-3)
+    idx = np.arange(m ** 3, dtype=np.int64)
+    rate = np.full(m ** 3, aB * n * n * x_eq ** 2 * dx ** 3)
+    run = dict(nx=m, ny=m, nz=m, dx=dx, c=W.C_LIGHT, dt=W.cfl_dt(dx), bc="periodic",
+               sigma_n=W.SIGMA, sigma_e=W.SIGMA, e_gamma_eV=W.E_GAMMA_EV)
+    a = A.from_workload(st, idx, rate, run, fixed_T=1, coll_ion=0)
+    try:
+        a.step(3000)
+        assert a.synchronize() == 0
+        f = a.get_fields()
+        b = a.photon_budget()
+    finally:
+        a.close()
+    print("x range", float(f["x"].min()), float(f["x"].max()))
+    assert np.allclose(f["x"], x_eq, rtol=2e-3, atol=0)
+    assert abs(budget_closure(b)) <= 1e-6
