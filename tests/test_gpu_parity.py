@@ -228,6 +228,13 @@ def test_error_paths():
     with pytest.raises(A.AtonError) as e:
         a.set_params(sub_eps=0.0)
     assert e.value.code == A.ERR_BADARG
+    for rows in (0, 3):
+        with pytest.raises(A.AtonError) as e:
+            a.set_tile_rows(rows)
+        assert e.value.code == A.ERR_BADARG
+    assert a.get_tile_rows() == 2          # the default: two rows per thread
+    a.set_tile_rows(1)
+    assert a.get_tile_rows() == 1
     a.close()
 
 
