@@ -114,15 +114,14 @@ struct Layout {
 // loop) and the halo rows over more cells. TO: transport only (the first kernel of the plain
 // three-kernel step): the transported and clamped (N, F) are stored, without sources or
 // chemistry, and y, T, nH are not read.
+// Launch bounds: the surrogate instance at tile 32 x 8 with two rows is held to five CTAs per SM,
+// like the exact one (its network tail after the z-loop would otherwise raise the register
+// count); the others declare no minimum (0): an explicit minimum of one CTA let the compiler
+// spend 127 registers on the exact two-row instance, four CTAs per SM, where it takes 94.
 template <int TY, bool PER, bool STD, bool FULL, bool HLL = false, bool SUR = false, int RPT = 1,
           bool TO = false>
-// (the surrogate instance at tile 32 x 8 with two rows is held to five CTAs per SM, like the
-// exact one: its network tail after the z-loop would otherwise raise the register count; the
-// others take no minimum (0): an explicit minimum of one CTA let the compiler spend 127
-// registers on the exact two-row instance, four CTAs per SM, where it takes 94 unbounded)
 __global__ void __launch_bounds__(kTileX * TY / RPT, (SUR && RPT == 2 && TY == 8) ? 5 : 0)
-    k_fused_tma(const FusedArgs A,
-                                                                 const __grid_constant__ TmaMaps M) {
+    k_fused_tma(const FusedArgs A, const __grid_constant__ TmaMaps M) {
   using L = Layout<TY, HLL>;
   constexpr int TX = kTileX, NH = 2 * TX + 2 * TY, TYT = TY / RPT;
   static_assert(TY % RPT == 0 && TX * TYT >= NH, "one halo slot per thread at most");
