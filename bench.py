@@ -275,14 +275,14 @@ def surrogate_leg(args):
             "ionised_atoms_rel_err": ion(su["x"]) / ion(ex["x"]) - 1,
             "max_abs_dx": float(np.abs(su["x"] - ex["x"]).max()),
             "budget_closure": su["clos"]}
-    res["front_cells_128"] = front_cells_leg(m, args)
+    res["front_cells_128"] = front_cells_leg(m)
     m.close()
     return {"path": "fused step, network in the same launch", "residual_max": 1e-4, "gate_substeps": 8.0,
             "train_records": int(rec.shape[0]), "pair_collection_seconds": t1 - t0,
             "train_seconds": t2 - t1, "train_steps": 3000, "batch": 16384, **res}
 
 
-def front_cells_leg(m, args):
+def front_cells_leg(m):
     """Where the exact operator sub-cycles heavily: a periodic 128^3 box whose every cell is
     drawn from the pair records of the exact operator that took >= 4 sub-steps, on lognormal
     boxes of the training recipe with seeds 300-303 (disjoint from training and evaluation);
