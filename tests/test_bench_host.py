@@ -28,4 +28,3 @@ def test_traffic_figures_are_bytes_per_cell_near_the_algorithmic_52():
     for key, b in bench.NCU_TRAFFIC.items():
         assert len(key) == 12
         assert 40.0 < b < 60.0
-
