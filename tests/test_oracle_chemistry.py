@@ -76,6 +76,47 @@ def test_recombination_cooling_energy_per_recombination():
             > O.cool_rec_B(1e5) / (O.alpha_B(1e5) * 1e5))
 
 
+def _kramers_milne_case_B(T, nmax=2000):
+    """Case-B recombination rate alpha_B [cm^3 s^-1] and kinetic-energy loss coefficient
+    beta_B [cm^3 s^-1, times kT] of hydrogen from first principles: Kramers' bound-free cross
+    section of level n (all l), sigma_n(nu) = 7.907e-18 n (nu_n/nu)^3 cm^2 (Gaunt factor 1),
+    turned into a recombination cross section by the Milne relation with g_n = 2 n^2, g_+ = 1,
+    sigma_rec = g_n (h nu / m_e c v)^2 sigma_n, and averaged over a Maxwellian. With
+    E = m_e v^2 / 2 and h nu = chi_n + E the Maxwellian integrals close in the exponential
+    integral: with x_n = chi_n / kT and s_n = exp(x_n) E1(x_n),
+      alpha_n = K n^3 chi_n^3 (kT)^-3/2 s_n,  beta_n = K n^3 chi_n^3 (kT)^-3/2 (1 - x_n s_n),
+    K = 2 sigma_0 sqrt(2/m_e) / (sqrt(pi) m_e c^2); case B sums n >= 2."""
+    from scipy.special import exp1
+    me, ry = 9.1093837e-28, 13.605693 * EV
+    kT = KB * T
+    n = np.arange(2, nmax + 1, dtype=np.float64)
+    chi = ry / n ** 2
+    x = chi / kT
+    s = np.exp(x) * exp1(x)
+    K = 2.0 * 7.907e-18 * math.sqrt(2.0 / me) / (math.sqrt(math.pi) * me * C ** 2)
+    pre = K * n ** 3 * chi ** 3 * kT ** -1.5
+    return float(np.sum(pre * s)), float(np.sum(pre * (1.0 - x * s)))
+
+
+def test_recombination_cooling_against_kramers_milne():
+    """The Hui & Gnedin (1997) case-B recombination-cooling fit against an independent
+    first-principles calculation (Kramers cross sections, Milne relation, Maxwellian; see
+    _kramers_milne_case_B). The mean kinetic energy carried off per recombination,
+    Lambda_B / (alpha_B kT), does not depend on the cross sections' normalisation and agrees
+    within 3 % from 3000 to 30 000 K (0.66 kT at 1e4 K); the energy-loss coefficient itself,
+    Lambda_B / kT, agrees with beta_B within 8 % (Gaunt factors near one for the excited
+    levels). A wrong exponent or divisor of the fit moves it far outside either window."""
+    for T in (3e3, 5e3, 1e4, 2e4, 3e4):
+        a_km, b_km = _kramers_milne_case_B(T)
+        lam = O.cool_rec_B(T)
+        assert lam / (O.alpha_B(T) * KB * T) == pytest.approx(b_km / a_km, rel=0.03), T
+        assert lam / (KB * T) == pytest.approx(b_km, rel=0.08), T
+    # the reference itself: Kramers' alpha_B is within 5 % of the textbook case-B values
+    for T, a in _table("osterbrock_alpha_B.txt"):
+        if 5e3 <= float(T) <= 2e4:
+            assert _kramers_milne_case_B(float(T))[0] == pytest.approx(float(a), rel=0.05)
+
+
 def test_heat_per_ionisation_from_paper_constants():
     g = {r[0]: float(r[1]) for r in _table("paper_constants.txt")}
     p = O.params(sigma_n=g["sigma_n"], sigma_e=g["sigma_e"], e_gamma_eV=g["e_gamma"])
