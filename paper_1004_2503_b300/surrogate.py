@@ -71,11 +71,8 @@ def train(mlp, records, dt, steps=2000, batch=8192, lr=1e-3, lr_end=5e-5, heavy_
     g = torch.Generator(device="cuda")
     g.manual_seed(seed)
     hist = []
-    uniform = heavy_weight == 1.0
     for k in range(steps):
-        # (equal weights: a uniform draw, much cheaper than multinomial over millions of weights)
-        sel = (torch.randint(0, X.shape[0], (batch,), device="cuda", generator=g) if uniform
-               else torch.multinomial(w, batch, replacement=True, generator=g))
+        sel = torch.multinomial(w, batch, replacement=True, generator=g)
         lr_k = lr * (lr_end / lr) ** (k / max(1, steps - 1))
         want = log_every and (k % log_every == 0 or k == steps - 1)
         loss = mlp.train_step(X[sel].contiguous(), T[sel].contiguous(), lr_k, want_loss=bool(want))
