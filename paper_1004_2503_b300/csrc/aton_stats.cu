@@ -139,8 +139,16 @@ __global__ void __launch_bounds__(kStatsThreads, kStatsBlocks / 148) k_stats(con
   const float4* __restrict__ gN = reinterpret_cast<const float4*>(a.N);
   const float4* __restrict__ gT = reinterpret_cast<const float4*>(a.T);
   const long long stride = (long long)gridDim.x * kStatsThreads;
-  for (long long g = (long long)blockIdx.x * kStatsThreads + t; g < n4; g += stride) {
-    const float4 n = __ldg(gn + g), yy = __ldg(gy + g), NN = __ldg(gN + g), TT = __ldg(gT + g);
+  // software-pipelined: the next group's four loads are issued before this group's bins and
+  // sums, so the loads of one iteration overlap the shared-memory work of the previous one
+  long long g = (long long)blockIdx.x * kStatsThreads + t;
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 qn = z4, qy = z4, qN = z4, qT = z4;
+  if (g < n4) { qn = __ldg(gn + g); qy = __ldg(gy + g); qN = __ldg(gN + g); qT = __ldg(gT + g); }
+  for (; g < n4; g += stride) {
+    const float4 n = qn, yy = qy, NN = qN, TT = qT;
+    const long long gq = g + stride;
+    if (gq < n4) { qn = __ldg(gn + gq); qy = __ldg(gy + gq); qN = __ldg(gN + gq); qT = __ldg(gT + gq); }
     int b[4], ky[4], kJ[4];
     b[0] = bins(n.x, yy.x, NN.x, ky[0], kJ[0]);
     b[1] = bins(n.y, yy.y, NN.y, ky[1], kJ[1]);
