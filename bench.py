@@ -57,6 +57,9 @@ NCU_TRAFFIC = {
     "e8a166fc6af2": (494.2208e6 + 360.033792e6) / 16777216,
     # the same code with the kernel's signature reflowed (its text without whitespace unchanged)
     "4f0cd4ebb515": (494.2208e6 + 360.033792e6) / 16777216,
+    # the same kernel; host code only: the transport-only instances' shared-memory attribute set
+    # per device with the others instead of on their first launch
+    "8a7101e6a1b5": (494.2208e6 + 360.033792e6) / 16777216,
 }
 
 

@@ -20,7 +20,9 @@
  *    that stream; aton_step does not.
  *  - Return 0 on success or a negative ATON_ERR_* code; aton_strerror() describes it and
  *    aton_last_message() gives the detail of the last failure on this thread.
- *  - A handle is not thread-safe; use one handle per host thread.
+ *  - A handle is not thread-safe; use one handle per host thread. Handles on different devices
+ *    may be created and used from different threads at once. A handle lives on the device that
+ *    was current at aton_init: make every call on it with that device current.
  */
 #ifndef ATON_H
 #define ATON_H

@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -23,6 +24,9 @@
 using namespace aton;
 
 static thread_local std::string g_msg;
+static constexpr int kMaxDevices = 64;
+static std::mutex g_attr_mutex;            // guards g_attr_done
+static bool g_attr_done[kMaxDevices] = {};  // kernel attributes set on device d
 
 static int fail(int code, const char* fmt, ...) {
   char buf[512];
@@ -698,15 +702,24 @@ int aton_init(int nx, int ny, int nz, double dx_cm, double c_cms, double dt_s, a
     return fail(ATON_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
   }
   h->device = dev;
-  static bool attrs_done = false;
-  if (!attrs_done) {
-    e = init_kernel_attributes();
-    if (e == cudaSuccess) e = init_tma_attributes();
-    if (e != cudaSuccess) {
-      delete h;
-      return fail(ATON_ERR_CUDA, "kernel attributes: %s", cudaGetErrorString(e));
+  // kernel attributes are per device: set them the first time a handle is made on this device
+  // (several host threads may create handles on different devices at once)
+  if (dev < 0 || dev >= kMaxDevices) {
+    delete h;
+    return fail(ATON_ERR_BADARG, "device index %d out of range", dev);
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    if (!g_attr_done[dev]) {
+      e = init_kernel_attributes();
+      if (e == cudaSuccess) e = init_tma_attributes();
+      if (e == cudaSuccess) e = init_stats_attributes();
+      if (e != cudaSuccess) {
+        delete h;
+        return fail(ATON_ERR_CUDA, "kernel attributes: %s", cudaGetErrorString(e));
+      }
+      g_attr_done[dev] = true;
     }
-    attrs_done = true;
   }
   auto bail = [&](int rc) { aton_finalize(h); return rc; };
   if (cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess)

@@ -249,14 +249,12 @@ __global__ void k_stats_final(const double* part_scalar, const double* part_bins
 
 }  // namespace
 
+cudaError_t init_stats_attributes() {
+  return cudaFuncSetAttribute(k_stats, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(StatsSmem));
+}
+
 cudaError_t launch_stats(const StatsArgs& a, double* out, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(k_stats, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)sizeof(StatsSmem));
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
   k_stats<<<kStatsBlocks, kStatsThreads, sizeof(StatsSmem), s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

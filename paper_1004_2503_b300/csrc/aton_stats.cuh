@@ -27,6 +27,10 @@ struct StatsArgs {
   unsigned long long* plateau_count;  // [1]
 };
 
+// The shared-memory attribute of k_stats on the current device (once per device, before the
+// first launch there).
+cudaError_t init_stats_attributes();
+
 // k_stats then the fixed-order sum of its slots into out[kStatsScalars + 2 kStatsMaxBins].
 cudaError_t launch_stats(const StatsArgs& a, double* out, cudaStream_t s);
 

@@ -464,15 +464,6 @@ cudaError_t launch_tma_t(const FusedArgs& a, const TmaMaps& m, cudaStream_t s) {
 
 }  // namespace
 
-cudaError_t init_tma_attributes() {
-  cudaError_t e;
-  if ((e = set_tma_attr<4, true>()) != cudaSuccess) return e;
-  if ((e = set_tma_attr<4, false>()) != cudaSuccess) return e;
-  if ((e = set_tma_attr<8, true>()) != cudaSuccess) return e;
-  if ((e = set_tma_attr<8, false>()) != cudaSuccess) return e;
-  if ((e = set_tma_attr<16, true>()) != cudaSuccess) return e;
-  return set_tma_attr<16, false>();
-}
 
 cudaError_t launch_fused_tma(int ty, int rpt, const FusedArgs& a, const TmaMaps& m,
                              cudaStream_t s) {
@@ -497,21 +488,35 @@ cudaError_t launch_fused_tma(int ty, int rpt, const FusedArgs& a, const TmaMaps&
 // three-kernel step: the plain step's transport pass, with one closure evaluation per cell.
 namespace {
 template <bool PER, bool FULL>
+cudaError_t set_to_attr() {
+  return cudaFuncSetAttribute(k_fused_tma<8, PER, false, FULL, false, false, 2, true>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Layout<8>::BYTES);
+}
+
+// (its shared-memory attribute is set per device with the others, init_tma_attributes)
+template <bool PER, bool FULL>
 cudaError_t launch_to(const FusedArgs& a, const TmaMaps& m, cudaStream_t s) {
   using K = Layout<8>;
-  static bool attr = false;   // (set once per process, before the first launch)
-  if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(
-        k_fused_tma<8, PER, false, FULL, false, false, 2, true>,
-        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::BYTES);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
   dim3 grid((a.P.nx + kTileX - 1) / kTileX, (a.P.ny + 7) / 8, (a.P.nz + a.tz - 1) / a.tz);
   k_fused_tma<8, PER, false, FULL, false, false, 2, true><<<grid, dim3(kTileX, 4), K::BYTES, s>>>(a, m);
   return cudaGetLastError();
 }
 }  // namespace
+
+// Shared-memory attributes of every instance of the TMA-staged kernel on the current device.
+cudaError_t init_tma_attributes() {
+  cudaError_t e;
+  if ((e = set_tma_attr<4, true>()) != cudaSuccess) return e;
+  if ((e = set_tma_attr<4, false>()) != cudaSuccess) return e;
+  if ((e = set_tma_attr<8, true>()) != cudaSuccess) return e;
+  if ((e = set_tma_attr<8, false>()) != cudaSuccess) return e;
+  if ((e = set_tma_attr<16, true>()) != cudaSuccess) return e;
+  if ((e = set_tma_attr<16, false>()) != cudaSuccess) return e;
+  if ((e = set_to_attr<true, true>()) != cudaSuccess) return e;
+  if ((e = set_to_attr<true, false>()) != cudaSuccess) return e;
+  if ((e = set_to_attr<false, true>()) != cudaSuccess) return e;
+  return set_to_attr<false, false>();
+}
 
 cudaError_t launch_transport_tma(const FusedArgs& a, const TmaMaps& m8, cudaStream_t s) {
   if (a.P.hll) return cudaErrorInvalidConfiguration;
