@@ -285,6 +285,46 @@ def surrogate_leg(args):
             "train_seconds": t2 - t1, "train_steps": 3000, "batch": 16384, **res}
 
 
+def front_cells_workload():
+    """The periodic 128^3 box of front-condition cells of the front-cells leg: every cell drawn
+    from the exact operator's records with at least four sub-steps on lognormal boxes of the
+    training recipe, seeds 300-303 (disjoint from training and evaluation); F = 0, no sources.
+    Returns (state, src_idx, src_rate, run, records)."""
+    from paper_1004_2503_b300 import surrogate as S
+    wl = list(S.training_boxes(range(300, 304), n=64, sigma_ln=1.5, nsrc=8))
+    rec = S.collect_pairs(wl, steps=120, stride=1, capacity=20_000_000, keep_light=0.0)
+    st, idx, rate, run = S.front_cells_box(rec, 128, wl[0][3], min_substeps=4)
+    return st, idx, rate, run, rec
+
+
+def front_cells_step():
+    """One exact plain step on the front-cells box, inside the NVTX start/end range
+    'front_cells_exact_step' (for an ncu capture filtered to its chemistry pass); prints one
+    JSON line with its CUDA-event time and the sub-steps per cell."""
+    import torch
+    from paper_1004_2503_b300 import aton as A
+    st, idx, rate, run, _ = front_cells_workload()
+    torch.cuda.empty_cache()   # (the pair records are dropped: little device memory in the capture)
+    a = A.from_workload(st, idx, rate, run)
+    s = torch.cuda.Stream()
+    a.set_stream(s)
+    a.set_exec(A.MODE_UNFUSED, 0)
+    a.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    rid = torch.cuda.nvtx.range_start("front_cells_exact_step")
+    e0.record(s)
+    a.step(1)
+    e1.record(s)
+    e1.synchronize()
+    torch.cuda.nvtx.range_end(rid)
+    d = a.diag()
+    a.close()
+    print(json.dumps({"workload": "front_cells_128", "cells": st["N"].size,
+                      "ms_plain_step": e0.elapsed_time(e1),
+                      "substeps_per_cell": d["substeps_total"] / st["N"].size}), flush=True)
+
+
 def front_cells_leg(m):
     """Where the exact operator sub-cycles heavily: a periodic 128^3 box whose every cell is
     drawn from the pair records of the exact operator that took >= 4 sub-steps, on lognormal
@@ -295,10 +335,7 @@ def front_cells_leg(m):
     CTA)."""
     import torch
     from paper_1004_2503_b300 import aton as A
-    from paper_1004_2503_b300 import surrogate as S
-    wl = list(S.training_boxes(range(300, 304), n=64, sigma_ln=1.5, nsrc=8))
-    rec = S.collect_pairs(wl, steps=120, stride=1, capacity=20_000_000, keep_light=0.0)
-    st, idx, rate, run = S.front_cells_box(rec, 128, wl[0][3], min_substeps=4)
+    st, idx, rate, run, rec = front_cells_workload()
     ncell = st["N"].size
     out = {"cells": ncell, "records_ge4_substeps": int((rec[:, 7] >= 4).sum()),
            "records_gt1_substep": int(rec.shape[0])}
@@ -617,7 +654,13 @@ def main():
                     help="intercell flux: global Lax-Friedrichs (the paper's) or HLL")
     ap.add_argument("--kernel", default="tma", choices=["tma", "ldg"],
                     help="fused kernel used with --tile (the autotuner chooses otherwise)")
+    ap.add_argument("--front-cells-step", action="store_true",
+                    help="only one exact plain step on the front-cells box, inside an NVTX range "
+                         "(for a filtered ncu capture of its chemistry pass)")
     args = ap.parse_args()
+    if args.front_cells_step:
+        front_cells_step()
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     world, rank, local = dist_setup()
