@@ -132,9 +132,11 @@ void aton_default_params(aton_params* p);
  * (a reduced value is allowed) and radiative step dt_s, on the current CUDA device.
  * The explicit scheme needs dt < dx/c (section 2.2, Eq. 7); the unsplit 3-D Lax-Friedrichs
  * update used here is positive only for 3 c dt / dx <= 1, which is enforced.
- * Allocates the device state (double-buffered N, F; y, T, nH) and a stream.
+ * Allocates the device state (double-buffered N, F; y, T, nH) and a stream. The first handle
+ * made on a device also sets the kernels' shared-memory limits there (once per device).
  * Errors: BADARG (sizes < 1, cell count above 2^31-1, non-positive dx/c/dt, 3 c dt/dx > 1,
- * out == NULL), NOMEM, CUDA. On error *out is set to NULL. */
+ * out == NULL, a current device index of 64 or more), NOMEM, CUDA. On error *out is set to
+ * NULL. */
 int aton_init(int nx, int ny, int nz, double dx_cm, double c_cms, double dt_s, aton_handle* out);
 
 /* Releases every resource of the handle (NULL is ignored). */
