@@ -267,7 +267,7 @@ int aton_launches_per_step(aton_handle h, int* launches);
 int aton_photon_sum_static(const float* N, int64_t n, double cell_volume, double* out,
                            void* stream);
 
-/* ---- chemistry surrogate (spec learned part; not in the paper) ----
+/* ---- chemistry surrogate (a learned replacement of the chemistry sub-cycle; not in the paper) ----
  * A 5 -> 64 -> 64 -> 3 SiLU network on BF16 tensor cores (FP32 accumulation) that replaces the
  * sub-cycled chemistry operator Phi (Appendix Eq. A4) for cells that would sub-cycle heavily.
  * Features: (log10 nH, log10 y, log10 T, log10 N, log10 dt); targets: the changes of log10 y,
