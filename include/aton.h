@@ -136,10 +136,12 @@ void aton_default_params(aton_params* p);
  * made on a device also sets the kernels' shared-memory limits there (once per device).
  * Errors: BADARG (sizes < 1, cell count above 2^31-1, non-positive dx/c/dt, 3 c dt/dx > 1,
  * out == NULL, a current device index of 64 or more), NOMEM, CUDA. On error *out is set to
- * NULL. */
+ * NULL and everything allocated so far is released. For tests of that clean-up, the
+ * environment variable ATON_TEST_FAIL_ALLOC=k makes the k-th of the handle's 15 device
+ * allocations (counting from 0) fail with NOMEM without allocating. */
 int aton_init(int nx, int ny, int nz, double dx_cm, double c_cms, double dt_s, aton_handle* out);
 
-/* Releases every resource of the handle (NULL is ignored). */
+/* Releases every resource of the handle (NULL is ignored); the caller's current device is kept. */
 void aton_finalize(aton_handle h);
 
 /* Replaces the parameters. Validated (BADARG on out-of-range values). Takes effect at the

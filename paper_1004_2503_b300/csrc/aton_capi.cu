@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -655,6 +656,8 @@ const char* aton_last_message(void) { return g_msg.c_str(); }
 
 void aton_finalize(aton_handle h) {
   if (!h) return;
+  int prev = -1;   // the caller's current device, made current again at the end
+  if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
   cudaSetDevice(h->device);
   if (h->stream()) cudaStreamSynchronize(h->stream());
   drop_graphs(h);
@@ -676,6 +679,7 @@ void aton_finalize(aton_handle h) {
   if (h->bud_ev) cudaEventDestroy(h->bud_ev);
   if (h->own) cudaStreamDestroy(h->own);
   delete h;
+  if (prev >= 0) cudaSetDevice(prev);
 }
 
 int aton_init(int nx, int ny, int nz, double dx_cm, double c_cms, double dt_s, aton_handle* out) {
@@ -724,18 +728,31 @@ int aton_init(int nx, int ny, int nz, double dx_cm, double c_cms, double dt_s, a
   auto bail = [&](int rc) { aton_finalize(h); return rc; };
   if (cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess)
     return bail(fail(ATON_ERR_CUDA, "cudaStreamCreate failed"));
+  // Failure injection on the host for tests: ATON_TEST_FAIL_ALLOC=k makes the k-th device
+  // allocation below (counting from 0) report cudaErrorMemoryAllocation without allocating, so
+  // the clean-up of a partly built handle can be checked without exhausting the device.
+  const char* fa = std::getenv("ATON_TEST_FAIL_ALLOC");
+  const int fail_at = fa ? std::atoi(fa) : -1;
+  int nalloc = 0;
+  auto dalloc = [&](void** p, size_t bytes) {
+    if (nalloc++ == fail_at) {
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+  };
   const size_t fb = sizeof(float) * (size_t)ncell;
   for (int b = 0; b < 2; ++b)
     for (int q = 0; q < 4; ++q)
-      if (cudaMalloc(&h->f[b][q], fb) != cudaSuccess)
+      if (dalloc((void**)&h->f[b][q], fb) != cudaSuccess)
         return bail(fail(ATON_ERR_NOMEM, "cudaMalloc of %zu bytes failed", fb));
-  if (cudaMalloc(&h->y, fb) != cudaSuccess || cudaMalloc(&h->T, fb) != cudaSuccess ||
-      cudaMalloc(&h->nH, fb) != cudaSuccess)
+  if (dalloc((void**)&h->y, fb) != cudaSuccess || dalloc((void**)&h->T, fb) != cudaSuccess ||
+      dalloc((void**)&h->nH, fb) != cudaSuccess)
     return bail(fail(ATON_ERR_NOMEM, "cudaMalloc of %zu bytes failed", fb));
-  if (cudaMalloc(&h->d_part, sizeof(double) * kSumBlocks) != cudaSuccess ||
-      cudaMalloc(&h->d_out, sizeof(double) * 4) != cudaSuccess ||
-      cudaMalloc(&h->d_u64, sizeof(unsigned long long) * 5) != cudaSuccess ||
-      cudaMalloc(&h->d_bad, sizeof(unsigned int)) != cudaSuccess)
+  if (dalloc((void**)&h->d_part, sizeof(double) * kSumBlocks) != cudaSuccess ||
+      dalloc((void**)&h->d_out, sizeof(double) * 4) != cudaSuccess ||
+      dalloc((void**)&h->d_u64, sizeof(unsigned long long) * 5) != cudaSuccess ||
+      dalloc((void**)&h->d_bad, sizeof(unsigned int)) != cudaSuccess)
     return bail(fail(ATON_ERR_NOMEM, "cudaMalloc of reduction scratch failed"));
   h->tz = std::min(64, nz);
   // TMA maps of the fields (row pitch must be a multiple of 16 bytes: nx % 4 == 0)

@@ -238,6 +238,39 @@ def test_error_paths():
     a.close()
 
 
+def test_allocation_failure_in_init_releases_everything(monkeypatch):
+    """Host-side failure injection: each of aton_init's device allocations is made to fail in
+    turn (ATON_TEST_FAIL_ALLOC). Every attempt returns NOMEM, and no device memory is left
+    behind: the 256^3 grid's field buffers are 64 MiB each, far above the tolerance. A handle
+    made afterwards steps normally."""
+    import torch
+    torch.cuda.init()
+    st, idx, rate, run = W.workload_32()
+    n = 256
+    A.Aton(32, 32, 32, run["dx"], run["c"], run["dt"]).close()   # (kernels loaded on the device)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    failures = 0
+    for k in range(64):
+        monkeypatch.setenv("ATON_TEST_FAIL_ALLOC", str(k))
+        try:
+            a = A.Aton(n, n, n, run["dx"], run["c"], run["dt"])
+        except A.AtonError as e:
+            assert e.code == A.ERR_NOMEM, (k, str(e))
+            failures += 1
+            continue
+        a.close()          # k beyond the last allocation: the handle was built
+        break
+    assert failures == 15
+    monkeypatch.delenv("ATON_TEST_FAIL_ALLOC")
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) < 16 * 2 ** 20
+    a = A.from_workload(st, idx, rate, run)
+    a.step(2)
+    assert a.synchronize() == 0
+    a.close()
+
+
 def test_subcycle_cap_is_reported():
     st, idx, rate, run = W.workload_small()
     a = A.from_workload(st, idx, rate, run, max_sub=2)
