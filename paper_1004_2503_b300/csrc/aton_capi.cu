@@ -239,13 +239,18 @@ static int ensure_slots_n(aton_handle h, int need) {
   free_slots(h->slots);
   drop_graphs(h);
   Slots s;
-  CU(cudaMalloc(&s.acc, sizeof(double) * 3 * need));
-  CU(cudaMalloc(&s.sub, sizeof(unsigned long long) * need));
-  CU(cudaMalloc(&s.mx, sizeof(unsigned int) * need));
-  CU(cudaMalloc(&s.err, sizeof(unsigned int) * need));
-  CU(cudaMalloc(&s.nan, sizeof(unsigned int) * need));
-  CU(cudaMalloc(&s.timeout, sizeof(unsigned int)));
-  CU(cudaMalloc(&s.sur, sizeof(unsigned int) * need));
+  cudaError_t e;
+  if ((e = cudaMalloc(&s.acc, sizeof(double) * 3 * need)) != cudaSuccess ||
+      (e = cudaMalloc(&s.sub, sizeof(unsigned long long) * need)) != cudaSuccess ||
+      (e = cudaMalloc(&s.mx, sizeof(unsigned int) * need)) != cudaSuccess ||
+      (e = cudaMalloc(&s.err, sizeof(unsigned int) * need)) != cudaSuccess ||
+      (e = cudaMalloc(&s.nan, sizeof(unsigned int) * need)) != cudaSuccess ||
+      (e = cudaMalloc(&s.timeout, sizeof(unsigned int))) != cudaSuccess ||
+      (e = cudaMalloc(&s.sur, sizeof(unsigned int) * need)) != cudaSuccess) {
+    free_slots(s);   // (what was allocated before the failure)
+    return fail(e == cudaErrorMemoryAllocation ? ATON_ERR_NOMEM : ATON_ERR_CUDA,
+                "tally slots: %s", cudaGetErrorString(e));
+  }
   s.n = need;
   h->slots = s;
   cudaStream_t st = h->stream();
@@ -537,7 +542,10 @@ int aton_ionisation_stats(aton_handle h, const aton_stats_params* p, aton_stats*
     return fail(ATON_ERR_BADARG, "spectral_index must be finite and > -3");
   const size_t n_u64 = 2 * (size_t)MB * MB + MB + 1;
   const size_t n_out = kStatsScalars + 2 * MB;
-  if (!h->st_edges) {
+  if (!h->st_edges || !h->st_part || !h->st_out || !h->st_u64) {
+    // (all four or none: a call after a failed allocation starts over)
+    cudaFree(h->st_edges); cudaFree(h->st_part); cudaFree(h->st_out); cudaFree(h->st_u64);
+    h->st_edges = nullptr; h->st_part = nullptr; h->st_out = nullptr; h->st_u64 = nullptr;
     CU(cudaMalloc(&h->st_edges, sizeof(float) * 3 * (MB + 1)));
     CU(cudaMalloc(&h->st_part, sizeof(double) * kStatsBlocks * (kStatsScalars + 2 * MB)));
     CU(cudaMalloc(&h->st_out, sizeof(double) * n_out));
